@@ -1,0 +1,335 @@
+"""Benchmark: Torontonian subset-terms/s at N = 24 on one GB300 (FP64 per-term arithmetic).
+
+Workload (one step): the click probability of one 24-click pattern of the
+200-mode pure state with uniform squeezing r = 0.8 behind a Haar-random
+interferometer (seed 1), i.e. 2^24 subset determinants of up to 48 x 48
+matrices, their alternating sum and p = Tor / sqrt(det Sigma).  The state is
+resident on the device when the timed region starts; the 24 click modes come
+from the host each step.
+
+Output: one JSON line (rank 0).  `value` is device time (CUDA events around
+each step on the library's stream); `e2e` runs the same step through the public
+API from pinned host buffers (state build from U, r included) with wall-clock
+timing; `roofline` is the dominant kernel (the register depth-first leaf
+kernel) against the FP64 rate measured in the same run; `cpu_baseline` is the
+oracle timed on this host's cores on a bounded sample.
+
+`--impl reference` times the oracle itself (the only reference there is: the
+paper's code is not available and ran on Titan CPUs) on a bounded sample.
+Multi-GPU (torchrun): independent replicas, no collective in the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Tor subset-terms/s (FP64, N=24)"
+UNIT = "subset-terms/s"
+
+
+def sym(d):
+    return d * (d + 1) // 2
+
+
+def tree_flops(q: int, complex_basis: bool) -> int:
+    """FP64 flops of the depth-first tree below one node with q undecided modes,
+    counted from the kernel's formulation: an FMA counts 2, a multiply, add or
+    inverse square root 1.  Per included pivot: det P, rsqrt, the scaled inverse,
+    L = u P^-1 for each of the 2q-2 rows below, and the rank-2 update of the
+    lower triangle of the (2q-2)^2 Schur complement.  Leaves add their term to
+    three accumulators."""
+    if q == 1:
+        return 11 if complex_basis else 9
+    d = 2 * q - 2
+    if complex_basis:
+        node = 12 + 20 * d + 16 * (sym(d) - d) + 8 * d
+    else:
+        node = 10 + 6 * d + 4 * sym(d)
+    return node + 2 * tree_flops(q - 1, complex_basis)
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = max(smax, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(ws, x: float, local: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda:%d" % local)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(n_sample: int):
+    """Oracle subset-terms/s on this host: the decision-tree oracle (~212-bit) on
+    the first n_sample modes of the N = 24 pattern."""
+    import gbs_inputs as gi
+    import oracle
+    st, modes = gi.single_large_torontonian_workload()
+    Sig = oracle.sigma(oracle.covariance(st.U, st.r, st.eta))
+    H = oracle.sigma_inv_block(Sig, modes[:n_sample])
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.torontonian(H, "tree", nthreads=threads)
+    dt = time.perf_counter() - t0
+    return (2 ** n_sample) / dt, dt, threads
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n_sample = args.ref_sample
+    for _ in range(args.warmup):
+        cpu_oracle_rate(min(n_sample, 12))
+    rates, total = [], 0.0
+    for _ in range(args.steps):
+        r, dt, threads = cpu_oracle_rate(n_sample)
+        rates.append(r)
+        total += dt
+    value = (2 ** n_sample) * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "qd (~212-bit)",
+        "data": "synthetic",
+        "config": {"workload": "Torontonian of the 200-mode r=0.8 Haar state (seed 1), first %d of its 24 click "
+                               "modes (bounded sample of the N=24 workload)" % n_sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "N=%d sub-pattern, 2^%d terms per step" % (n_sample, n_sample)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "dd", "td", "fp32"])
+    ap.add_argument("--basis", default="real", choices=["real", "complex"])
+    ap.add_argument("--N", type=int, default=24)
+    ap.add_argument("--cpu-sample", type=int, default=19, help="click count of the oracle's CPU sample")
+    ap.add_argument("--ref-sample", type=int, default=16, help="click count per step of --impl reference")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+
+    import gbs_inputs as gi
+    from paper_1810_00900_gb300 import build as gbs_build
+
+    if local == 0:
+        gbs_build.build()
+    barrier(ws)
+    import paper_1810_00900_gb300 as gbs
+
+    dev = local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = gbs.Context(dev)
+    ctx.set_stream(stream.cuda_stream)
+    peak_gflops = ctx.measure_fp64_peak()
+
+    st_p, modes24 = gi.single_large_torontonian_workload(args.N)
+    modes = np.ascontiguousarray(modes24, dtype=np.int32)
+    st = gbs.build_state(ctx, st_p.U, st_p.r, st_p.eta)
+    complex_basis = args.basis == "complex"
+    Q = {("fp64", False): 5, ("fp64", True): 4, ("dd", False): 4, ("dd", True): 3, ("td", False): 3,
+         ("td", True): 2, ("fp32", False): 5, ("fp32", True): 4}[(args.prec, complex_basis)]
+    Q = min(Q, args.N)
+    depth = args.N - Q
+    leaf_flops = (2 ** depth) * tree_flops(Q, complex_basis)
+    total_flops = tree_flops(args.N, complex_basis)
+
+    # L2 flush buffer (larger than the 129 MB L2), written between timed steps.
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda:%d" % dev)
+
+    def step():
+        return gbs.torontonian(ctx, st, modes, args.prec, args.basis)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.kernel_time()  # reset
+    ctx.enable_timing(True)
+    launches0 = ctx.launch_count
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(dev)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    results = []
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+        results.append(step())
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    launches = ctx.launch_count - launches0
+    ctx.enable_timing(False)
+    leaf_ms, leaf_n = ctx.kernel_time()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    dev_ms = allreduce_max(ws, dev_ms, local)
+    terms = float(2 ** args.N)
+    value = ws * args.steps * terms / (dev_ms * 1e-3)
+    leaf_avg_s = leaf_ms / max(leaf_n, 1) * 1e-3
+    achieved = leaf_flops / leaf_avg_s / 1e12
+    peak = peak_gflops / 1e3
+
+    # e2e: the same step through the public API from pinned host buffers, state build included.
+    U_pin = torch.empty((st_p.M, st_p.M), dtype=torch.complex128, pin_memory=True)
+    U_pin.numpy()[:] = st_p.U
+    r_pin = torch.empty(st_p.M, dtype=torch.float64, pin_memory=True)
+    r_pin.numpy()[:] = st_p.r
+    for _ in range(2):
+        s2 = gbs.build_state(ctx, U_pin.numpy(), r_pin.numpy(), st_p.eta)
+        gbs.torontonian(ctx, s2, modes, args.prec, args.basis)
+        s2.free()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        s2 = gbs.build_state(ctx, U_pin.numpy(), r_pin.numpy(), st_p.eta)
+        pr = gbs.torontonian(ctx, s2, modes, args.prec, args.basis)
+        s2.free()
+    e2e_s = allreduce_max(ws, time.perf_counter() - t0, local)
+    e2e_value = ws * args.steps * terms / e2e_s
+    h2d = st_p.M * st_p.M * 16 + st_p.M * 8 + modes.nbytes
+    d2h = 8 * 16  # the probability record
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.prec == "fp64" else args.prec, "data": "synthetic",
+        "config": {
+            "workload": "single Torontonian, N=%d clicks of the M=200 pure state (r=0.8, Haar seed 1): "
+                        "2^%d subset determinants per step" % (args.N, args.N),
+            "M": 200, "N": args.N, "basis": args.basis, "per_term_arithmetic": args.prec,
+            "sum": "double-double" if args.prec in ("fp64", "dd", "fp32") else "triple-double",
+            "l2": "flushed between steps (256 MB write); tree level buffers also exceed L2",
+            "parallelism": "replicas" if ws > 1 else "single GPU",
+        },
+        "roofline": {
+            "bound": "alu", "kernel": "tree_leaf_kernel (register depth-first, last %d levels)" % Q,
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": "FP64 DFMA-chain kernel measured in this run (gbs_measure_fp64_peak)",
+            "traffic": None, "flops_per_launch": leaf_flops, "leaf_ms_avg": leaf_avg_s * 1e3,
+            "step_flops": total_flops,
+            "step_tflops": total_flops * args.steps / (dev_ms * 1e-3) / 1e12,
+        },
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "result": {"p": results[-1].p, "kappa": results[-1].kappa, "prec": results[-1].prec},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rate, dt, threads = cpu_oracle_rate(args.cpu_sample)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": "N=%d sub-pattern of the same state (2^%d terms, %.1f s, ~212-bit "
+                                          "decision-tree oracle)" % (args.cpu_sample, args.cpu_sample, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    st.free()
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * gbs.h -- C ABI of libgbs: exact threshold-detector Gaussian Boson Sampling
+ * (click probabilities via Torontonians and chain-rule click sampling) on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Gupt, Arrazola, Quesada, Bromley, "Classical benchmarking of Gaussian
+ * Boson Sampling on the Titan supercomputer", arXiv:1810.00900.  Sec. II gives
+ * the sequential-measurement algorithm: a Gaussian state (Eq. 1), the
+ * no-click update V_A' = V_A - V_AB (V_B + 1)^-1 V_AB^T (Eq. 4a), the vacuum
+ * probability q = 2 / sqrt(det(V_B + 1)) of a measured mode (Eq. 5) and the
+ * click / no-click mixture updates (Eqs. 6-7).  Summing that mixture in closed
+ * form gives the threshold click probability of a pattern S (clicks on S,
+ * vacuum elsewhere) as
+ *
+ *     p(S) = Tor(O_S) / sqrt(det Sigma),
+ *     Tor(O_S) = sum over Z subset S of (-1)^(|S|-|Z|) / sqrt(det(1 - O_Z)),
+ *
+ * with Sigma = V + 1/2 (complex basis, vacuum V = 1/2) and O = 1 - Sigma^-1, so
+ * that every term is a vacuum probability of Eq. (5).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  - Modes are 0-based.  M = number of modes of a state, N = number of clicks.
+ *  - Complex numbers are interleaved (re, im) doubles.  Matrices are row-major.
+ *  - Complex basis: (a_1..a_M, a_1^+..a_M^+) ("block order"); covariance V is
+ *    2M x 2M complex with vacuum V = I/2.  The paper's real basis is
+ *    (x_1, p_1, ..., x_M, p_M) with hbar = 2; a = (x + i p)/2.
+ *  - Status: every function returns a gbs_status (0 = GBS_OK).  No exceptions
+ *    cross the ABI.  On error the outputs are left unspecified and a message
+ *    is available from gbs_ctx_last_error().
+ *  - Ownership: the caller owns every array it passes (host memory unless a
+ *    parameter says "device"); the library copies what it keeps.  Handles
+ *    (gbs_ctx, gbs_state) are owned by the caller and freed explicitly.
+ *  - Thread safety: calls on one context are serialised internally; the
+ *    request loop (gbs_submit / gbs_poll) may be used from any thread.
+ */
+#ifndef GBS_H_
+#define GBS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gbs_status;
+#define GBS_OK 0
+#define GBS_EINVAL 1      /* invalid argument */
+#define GBS_ENOMEM 2      /* device memory budget of the context exceeded */
+#define GBS_ENOTPD 3      /* a matrix that must be positive definite is not */
+#define GBS_EPRECISION 4  /* the requested accuracy cannot be certified */
+#define GBS_EREJECT 5     /* postselection attempts exhausted */
+#define GBS_ETIMEDOUT 6   /* a bounded wait ran out */
+#define GBS_ECUDA 7       /* a CUDA runtime call failed */
+#define GBS_PENDING 8     /* request not finished yet (gbs_poll) */
+#define GBS_ENOTFOUND 9   /* unknown ticket */
+
+/* Per-term arithmetic of the subset enumeration. */
+typedef enum {
+  GBS_PREC_AUTO = 0,      /* cheapest of FP64 / DD / TD whose error estimate meets rel_tol */
+  GBS_PREC_FP64 = 1,      /* IEEE double */
+  GBS_PREC_DD = 2,        /* double-double, ~106-bit significand */
+  GBS_PREC_TD = 3,        /* triple-double, ~159-bit significand */
+  GBS_PREC_FP32_DIAG = 4  /* FP32 terms, FP64 sums: diagnostic only */
+} gbs_prec;
+
+/* Basis of the matrices the enumeration factors.  Both give identical
+ * determinants (the per-mode change of basis is unitary); the real one needs
+ * a quarter of the floating-point work. */
+typedef enum { GBS_BASIS_AUTO = 0, GBS_BASIS_REAL = 1, GBS_BASIS_COMPLEX = 2 } gbs_basis;
+
+typedef struct gbs_ctx gbs_ctx;
+typedef struct gbs_state gbs_state;
+
+/* Result of a probability evaluation. */
+typedef struct {
+  double p_hi, p_lo;     /* p(S) = p_hi + p_lo */
+  double tor[3];         /* Tor(O_S) = tor[0] + tor[1] + tor[2] */
+  double abs_sum;        /* sum over the 2^N subsets of |term| */
+  double kappa;          /* cancellation ratio abs_sum / |Tor| */
+  double err_bound;      /* estimated absolute error of p (model: 4 N u abs_sum / sqrt(det Sigma)) */
+  double logdet_sigma;   /* log det Sigma of the state */
+  int prec_used;         /* gbs_prec that produced the value */
+  int basis_used;        /* gbs_basis that produced the value */
+} gbs_prob;
+
+/* ------------------------------------------------------------ context -- */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the device
+ * memory the context may hold (0 = no bound); allocations beyond it fail with
+ * GBS_ENOMEM.  The context owns a CUDA stream unless gbs_ctx_set_stream is used. */
+gbs_status gbs_ctx_create(gbs_ctx** ctx, int device, size_t hbm_budget_bytes);
+void gbs_ctx_destroy(gbs_ctx* ctx);
+/* Run all later work of the context on `cuda_stream` (a cudaStream_t, borrowed). */
+gbs_status gbs_ctx_set_stream(gbs_ctx* ctx, void* cuda_stream);
+const char* gbs_ctx_last_error(const gbs_ctx* ctx);
+const char* gbs_status_string(gbs_status st);
+/* Device bytes currently held by the context and its states. */
+size_t gbs_ctx_bytes_in_use(const gbs_ctx* ctx);
+/* Kernel launches made by the context so far (all entry points). */
+long long gbs_ctx_launch_count(const gbs_ctx* ctx);
+/* When enabled, the subset-enumeration kernel of every Torontonian is bracketed
+ * by CUDA events on the context stream; gbs_ctx_kernel_time returns the summed
+ * device time (ms) and the number of timed launches, and resets them. */
+gbs_status gbs_ctx_enable_timing(gbs_ctx* ctx, int enable);
+gbs_status gbs_ctx_kernel_time(gbs_ctx* ctx, double* total_ms, long long* launches);
+
+/* FP64 throughput of this GPU, measured now: a full grid of independent
+ * dependent-FMA chains (no memory traffic), best of three timed launches on the
+ * context stream.  *gflops receives the rate in GFLOP/s (one FMA = 2 flops).
+ * The denominator of the FP64 roofline of the subset enumeration.  The paper
+ * has no GPU counterpart; it reports CPU walltimes only (Sec. III, Table II). */
+gbs_status gbs_measure_fp64_peak(gbs_ctx* ctx, double* gflops);
+
+/* -------------------------------------------------------------- states -- */
+
+/* Build the state of M single-mode squeezers r[0..M-1] followed by the M x M
+ * interferometer U (complex, row-major) and uniform loss with transmissivity
+ * eta in (0, 1].  Paper Sec. II (Eq. 1) for the state, Sec. III ("8 dB of
+ * squeezing", Haar-random unitaries) for the inputs, Sec. IV for losses.
+ *   V = S S^+ / 2,  S = [[U ch R, U sh R], [U* sh R, U* ch R]],  R = diag(r),
+ *   then V <- eta V + (1 - eta) I/2.
+ * V_out (may be NULL): caller-owned 2M x 2M complex, receives V in block order.
+ * *st receives a library-owned handle keeping U, r, eta and V on the device.
+ * Errors: GBS_EINVAL (M < 1, eta outside (0, 1], non-finite input),
+ * GBS_ENOMEM, GBS_ECUDA. */
+gbs_status gbs_build_state(gbs_ctx* ctx, int M, const double* U, const double* r, double eta, double* V_out,
+                           gbs_state** st);
+
+/* A state given only by its 2M x 2M complex covariance V (block order, host).
+ * Sigma = V + I/2 is inverted once on the device (Gauss-Jordan, FP64).
+ * Errors: GBS_EINVAL, GBS_ENOTPD (Sigma not positive definite), GBS_ENOMEM. */
+gbs_status gbs_state_from_V(gbs_ctx* ctx, int M, const double* V, gbs_state** st);
+void gbs_state_free(gbs_state* st);
+/* Number of modes and log det Sigma of a state. */
+gbs_status gbs_state_info(const gbs_state* st, int* M, double* logdet_sigma);
+
+/* (Sigma^-1)_S for the N modes `modes` (distinct, in [0, M)), mode-interleaved:
+ * rows/columns 2i, 2i+1 belong to modes[i].  basis GBS_BASIS_COMPLEX gives the
+ * (a_j, a_j^+) rows, 2N x 2N complex (8 N^2 doubles); GBS_BASIS_REAL the
+ * (x_j, p_j) rows, 2N x 2N real (4 N^2 doubles).  H_out is caller-owned host
+ * memory.  For states built from (U, r, eta) this is the closed form
+ * Sigma^-1 = E diag(1/d) E^+ restricted to S (O(N^2 M) work). */
+gbs_status gbs_sigma_inv_block(gbs_ctx* ctx, const gbs_state* st, const int* modes, int N, int basis,
+                               double* H_out);
+
+/* --------------------------------------------------------- probabilities -- */
+
+/* Click probability of the pattern "clicks on modes[0..N-1], no click on every
+ * other mode of the state", p = Tor(O_S)/sqrt(det Sigma).  The 2^N subset
+ * determinants run on the GPU (decision tree with shared-prefix Schur
+ * complements), the alternating sum is accumulated in double-double (or
+ * triple-double).  prec: gbs_prec; basis: gbs_basis; out: caller-owned.
+ * rel_tol (<= 0 means 1e-10) is the target relative error for GBS_PREC_AUTO.
+ * Errors: GBS_EINVAL (N < 0 or N > 32, repeated or out-of-range modes),
+ * GBS_ENOTPD, GBS_EPRECISION (AUTO could not meet rel_tol even in TD; *out then
+ * holds the TD value), GBS_ENOMEM, GBS_ECUDA. */
+gbs_status gbs_torontonian(gbs_ctx* ctx, const gbs_state* st, const int* modes, int N, int prec, int basis,
+                           double rel_tol, gbs_prob* out);
+
+/* Signed subset sum of an explicit matrix, the enumeration alone:
+ *   tor = sum over Z subset {0..n-1} of (-1)^(n-|Z|) det(G_Z)^(-1/2)
+ * split as tor = inc + exc by whether Z contains mode n-1, and abs_sum =
+ * sum of |terms|.  G: host, 2n x 2n, mode i on rows/columns 2i, 2i+1; complex
+ * interleaved (basis GBS_BASIS_COMPLEX) or real (GBS_BASIS_REAL), Hermitian /
+ * symmetric positive definite (only the lower triangle is read).
+ * inc, exc, tor: caller-owned double[3] each (may be NULL), unevaluated sums.
+ * prec must not be GBS_PREC_AUTO.  Errors: GBS_EINVAL, GBS_ENOTPD, GBS_ECUDA. */
+gbs_status gbs_subset_sum(gbs_ctx* ctx, int n, const double* G, int basis, int prec, double* inc, double* exc,
+                          double* tor, double* abs_sum);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBS_H_ */

@@ -1,0 +1,11 @@
+"""GB300-native exact threshold-detector Gaussian Boson Sampling.
+
+Click probabilities via Torontonians (the 2^N subset determinants enumerated on
+the GPU by a decision tree of shared-prefix Schur complements) and chain-rule
+click sampling, behind the C ABI in include/gbs.h.  This package is the thin
+Python binding; importing it does not touch the GPU.
+"""
+from ._lib import (  # noqa: F401
+    BASIS, PREC, Context, GbsError, Prob, State, build_state, header_functions, load, sigma_inv_block,
+    state_from_V, subset_sum, torontonian,
+)

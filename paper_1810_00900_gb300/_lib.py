@@ -1,0 +1,247 @@
+"""ctypes binding of libgbs (include/gbs.h): argument marshalling only.
+
+Every computation behind these functions runs in the library's CUDA kernels.
+There is no CPU fallback: if the shared library is missing, loading fails
+loudly (build it with ``paper_1810_00900_gb300.build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgbs.so")
+HEADER = os.path.join(HERE, "..", "include", "gbs.h")
+
+OK, EINVAL, ENOMEM, ENOTPD, EPRECISION, EREJECT, ETIMEDOUT, ECUDA, PENDING, ENOTFOUND = range(10)
+PREC = {"auto": 0, "fp64": 1, "dd": 2, "td": 3, "fp32": 4}
+PREC_NAME = {v: k for k, v in PREC.items()}
+BASIS = {"auto": 0, "real": 1, "complex": 2}
+BASIS_NAME = {v: k for k, v in BASIS.items()}
+
+
+class GbsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("gbs status %d: %s" % (status, msg))
+        self.status = status
+
+
+class gbs_prob(ctypes.Structure):
+    _fields_ = [
+        ("p_hi", ctypes.c_double), ("p_lo", ctypes.c_double), ("tor", ctypes.c_double * 3),
+        ("abs_sum", ctypes.c_double), ("kappa", ctypes.c_double), ("err_bound", ctypes.c_double),
+        ("logdet_sigma", ctypes.c_double), ("prec_used", ctypes.c_int), ("basis_used", ctypes.c_int),
+    ]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/gbs.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(gbs_\w+)\s*\(", txt, flags=re.M)))
+
+
+def load() -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libgbs.so is not built (%s); call paper_1810_00900_gb300.build.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "gbs_ctx_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t]),
+        "gbs_ctx_destroy": (None, [_vp]),
+        "gbs_ctx_set_stream": (ctypes.c_int, [_vp, _vp]),
+        "gbs_ctx_last_error": (ctypes.c_char_p, [_vp]),
+        "gbs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "gbs_ctx_bytes_in_use": (ctypes.c_size_t, [_vp]),
+        "gbs_ctx_launch_count": (ctypes.c_longlong, [_vp]),
+        "gbs_ctx_enable_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "gbs_ctx_kernel_time": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+        "gbs_measure_fp64_peak": (ctypes.c_int, [_vp, _dp]),
+        "gbs_build_state": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, ctypes.POINTER(_vp)]),
+        "gbs_state_from_V": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(_vp)]),
+        "gbs_state_free": (None, [_vp]),
+        "gbs_state_info": (ctypes.c_int, [_vp, _ip, _dp]),
+        "gbs_sigma_inv_block": (ctypes.c_int, [_vp, _vp, _ip, ctypes.c_int, ctypes.c_int, _dp]),
+        "gbs_torontonian": (ctypes.c_int, [_vp, _vp, _ip, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_double, ctypes.POINTER(gbs_prob)]),
+        "gbs_subset_sum": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a: np.ndarray):
+    return a.ctypes.data_as(_ip)
+
+
+class Context:
+    """A libgbs context on one CUDA device (owns a stream and a workspace)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.L = load()
+        h = _vp()
+        st = self.L.gbs_ctx_create(ctypes.byref(h), device, hbm_budget_bytes)
+        if st:
+            raise GbsError(st, "gbs_ctx_create failed (device %d)" % device)
+        self.h = h
+
+    def check(self, st: int):
+        if st:
+            raise GbsError(st, self.L.gbs_ctx_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.gbs_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream_handle: int):
+        self.check(self.L.gbs_ctx_set_stream(self.h, _vp(stream_handle)))
+
+    @property
+    def bytes_in_use(self) -> int:
+        return int(self.L.gbs_ctx_bytes_in_use(self.h))
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.L.gbs_ctx_launch_count(self.h))
+
+    def enable_timing(self, on: bool = True):
+        self.check(self.L.gbs_ctx_enable_timing(self.h, 1 if on else 0))
+
+    def measure_fp64_peak(self) -> float:
+        """Measured FP64 rate of the device in GFLOP/s."""
+        g = ctypes.c_double()
+        self.check(self.L.gbs_measure_fp64_peak(self.h, ctypes.byref(g)))
+        return g.value
+
+    def kernel_time(self):
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        self.check(self.L.gbs_ctx_kernel_time(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+
+class State:
+    def __init__(self, ctx: Context, h, M: int):
+        self.ctx, self.h, self.M = ctx, h, M
+
+    def free(self):
+        if self.h:
+            self.ctx.L.gbs_state_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def logdet_sigma(self) -> float:
+        m = ctypes.c_int()
+        ld = ctypes.c_double()
+        self.ctx.check(self.ctx.L.gbs_state_info(self.h, ctypes.byref(m), ctypes.byref(ld)))
+        return ld.value
+
+
+def build_state(ctx: Context, U, r, eta: float = 1.0, want_V: bool = False):
+    U = np.ascontiguousarray(U, dtype=np.complex128)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    M = r.shape[0]
+    if U.shape != (M, M):
+        raise ValueError("U must be M x M")
+    V = np.empty((2 * M, 2 * M), dtype=np.complex128) if want_V else None
+    h = _vp()
+    ctx.check(ctx.L.gbs_build_state(ctx.h, M, _p(U.view(np.float64)), _p(r), float(eta),
+                                    _p(V.view(np.float64)) if want_V else None, ctypes.byref(h)))
+    st = State(ctx, h, M)
+    return (st, V) if want_V else st
+
+
+def state_from_V(ctx: Context, V) -> State:
+    V = np.ascontiguousarray(V, dtype=np.complex128)
+    M = V.shape[0] // 2
+    h = _vp()
+    ctx.check(ctx.L.gbs_state_from_V(ctx.h, M, _p(V.view(np.float64)), ctypes.byref(h)))
+    return State(ctx, h, M)
+
+
+def sigma_inv_block(ctx: Context, st: State, modes, basis: str = "complex") -> np.ndarray:
+    m = np.ascontiguousarray(modes, dtype=np.int32)
+    N = m.size
+    real = basis == "real"
+    out = np.zeros((2 * N, 2 * N), dtype=np.float64 if real else np.complex128)
+    ctx.check(ctx.L.gbs_sigma_inv_block(ctx.h, st.h, _i(m) if N else None, N, BASIS[basis],
+                                        _p(out.view(np.float64)) if N else _p(np.zeros(1))))
+    return out
+
+
+@dataclass
+class Prob:
+    p: float
+    p_lo: float
+    tor: tuple
+    abs_sum: float
+    kappa: float
+    err_bound: float
+    logdet_sigma: float
+    prec: str
+    basis: str
+
+    @property
+    def tor_value(self) -> float:
+        return self.tor[0] + (self.tor[1] + self.tor[2])
+
+
+def torontonian(ctx: Context, st: State, modes, prec: str = "auto", basis: str = "auto",
+                rel_tol: float = 0.0) -> Prob:
+    m = np.ascontiguousarray(modes, dtype=np.int32)
+    out = gbs_prob()
+    ctx.check(ctx.L.gbs_torontonian(ctx.h, st.h, _i(m) if m.size else None, int(m.size), PREC[prec], BASIS[basis],
+                                    float(rel_tol), ctypes.byref(out)))
+    return Prob(out.p_hi, out.p_lo, tuple(out.tor), out.abs_sum, out.kappa, out.err_bound, out.logdet_sigma,
+                PREC_NAME[out.prec_used], BASIS_NAME[out.basis_used])
+
+
+def subset_sum(ctx: Context, G, basis: str = "complex", prec: str = "fp64"):
+    """Signed subset sum of an explicit matrix (see gbs_subset_sum): (inc, exc, tor, abs_sum)."""
+    real = basis == "real"
+    G = np.ascontiguousarray(G, dtype=np.float64 if real else np.complex128)
+    n = G.shape[0] // 2
+    inc, exc, tor = np.zeros(3), np.zeros(3), np.zeros(3)
+    a = ctypes.c_double()
+    ctx.check(ctx.L.gbs_subset_sum(ctx.h, n, _p(G.view(np.float64)), BASIS[basis], PREC[prec], _p(inc), _p(exc),
+                                   _p(tor), ctypes.byref(a)))
+    return inc, exc, tor, a.value

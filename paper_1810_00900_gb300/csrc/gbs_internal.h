@@ -1,0 +1,107 @@
+// Internal C++ interfaces shared by the translation units of libgbs.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/gbs.h"
+
+namespace gbs {
+
+struct TreeOut;
+
+// Device memory obtained by the library, accounted against the context budget.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct KernelTimer {
+  cudaEvent_t start = nullptr, stop = nullptr;
+  double total_ms = 0.0;
+  long long count = 0;
+  bool pending = false;
+};
+
+}  // namespace gbs
+
+struct gbs_ctx {
+  int device = 0;
+  size_t budget = 0;
+  std::atomic<size_t> in_use{0};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string last_error;
+  std::mutex mu;  // serialises calls that use the shared workspace
+
+  // tree workspace (grown on demand)
+  gbs::DevBuf lvl[2], sbuf[2], partials, out, status, hbuf;
+  // host-pinned readback
+  void* host_out = nullptr;
+
+  // instrumentation
+  bool timing = false;
+  gbs::KernelTimer leaf_timer;
+  std::atomic<long long> launches{0};
+  int sm_count = 0;
+
+  // request loop (see gbs_server.cu)
+  void* server = nullptr;
+};
+
+struct gbs_state {
+  gbs_ctx* ctx = nullptr;
+  int M = 0;
+  bool has_factors = false;  // built from (U, r, eta): closed-form Sigma^-1 blocks available
+  double eta = 1.0;
+  double logdet_sigma = 0.0;
+  gbs::DevBuf U;      // M x M complex (interleaved), row-major
+  gbs::DevBuf r;      // M doubles
+  gbs::DevBuf alpha;  // M doubles: (1/d+ + 1/d-)/2
+  gbs::DevBuf beta;   // M doubles: (1/d+ - 1/d-)/2
+  gbs::DevBuf V;      // 2M x 2M complex covariance, block order (a, a^+)
+  gbs::DevBuf Sinv;   // 2M x 2M complex Sigma^-1 (states given by V only)
+};
+
+namespace gbs {
+
+// error helpers (gbs_api.cu)
+gbs_status set_error(gbs_ctx* ctx, gbs_status st, const std::string& msg);
+gbs_status check_cuda(gbs_ctx* ctx, cudaError_t e, const char* what);
+gbs_status dev_alloc(gbs_ctx* ctx, DevBuf& b, size_t bytes);
+gbs_status dev_reserve(gbs_ctx* ctx, DevBuf& b, size_t bytes);  // grow-only
+void dev_free(gbs_ctx* ctx, DevBuf& b);
+inline void count_launch(gbs_ctx* ctx, long long n = 1) { ctx->launches += n; }
+
+// Tree drivers (tree_*.cu).  G: packed lower-triangular root matrix on the
+// device (2n x 2n, entry tri(a, b) at index tri(a, b)), element type matching
+// the variant (double, double2 = complex, dd, ...), already mode-interleaved.
+// Results land in the device TreeOut *out and are NOT synchronised.
+gbs_status tree_fp64_real(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
+gbs_status tree_fp64_cplx(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
+gbs_status tree_dd_real(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
+gbs_status tree_dd_cplx(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
+gbs_status tree_td_real(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
+gbs_status tree_td_cplx(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
+gbs_status tree_fp32_real(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
+gbs_status tree_fp32_cplx(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
+
+// Up to 32 click modes passed by value as a kernel argument.
+struct ModeList {
+  int m[32];
+};
+
+// Request loop (gbs_server.cu): stop and free it, if running.
+void server_shutdown(gbs_ctx* ctx);
+
+// States (gbs_state.cu)
+gbs_status state_build(gbs_ctx* ctx, int M, const double* U, const double* r, double eta, double* V_out,
+                       gbs_state** out);
+gbs_status state_from_V(gbs_ctx* ctx, int M, const double* V, gbs_state** out);
+// Enqueue the packed lower triangle of (Sigma^-1)_S (FP64; complex entries as
+// (re, im) pairs, or real x/p entries) into dev_out on the context stream.
+gbs_status click_block(gbs_ctx* ctx, const gbs_state* st, const int* modes, int N, int real_basis, void* dev_out);
+}  // namespace gbs

@@ -1,0 +1,235 @@
+// Device number types for the subset-determinant tree.
+//
+// The Torontonian's alternating sum cancels by a factor kappa = sum|t| / |Tor|
+// that reaches 1e20 and beyond for 20+ clicks, so the per-term arithmetic comes
+// in several widths:
+//   double          FP64 (the throughput kernel)
+//   dd              double-double, ~106 bits
+//   td              triple-double, ~159 bits
+//   float           FP32, only to measure where it breaks down
+// and each can be real (symmetric matrices in the paper's x/p basis) or
+// complex (Hermitian matrices in the a/a^+ basis).
+//
+// The extended types are unevaluated sums of doubles built from error-free
+// transformations: TwoSum (Knuth, TAOCP vol. 2), FastTwoSum (Dekker 1971) and
+// TwoProd by fused multiply-add.  Addition is the "sloppy" kind: its error is
+// bounded relative to the operands, which is what the tree needs (entries and
+// terms are O(1); the final sum's cancellation is paid for by the width).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+#define GBS_HD __host__ __device__ __forceinline__
+
+namespace gbs {
+
+// ------------------------------------------------------------- EFTs ------
+GBS_HD void two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  double bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+GBS_HD void fast_two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+GBS_HD void two_prod(double a, double b, double& p, double& e) {
+  p = a * b;
+  e = fma(a, b, -p);
+}
+
+// ---------------------------------------------------------- double-double --
+struct dd {
+  double hi, lo;
+};
+GBS_HD dd dd_make(double a) { return dd{a, 0.0}; }
+GBS_HD dd operator-(dd a) { return dd{-a.hi, -a.lo}; }
+GBS_HD dd operator+(dd a, dd b) {
+  double s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e += a.lo + b.lo;
+  dd r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+GBS_HD dd operator-(dd a, dd b) { return a + (-b); }
+GBS_HD dd operator*(dd a, dd b) {
+  double p, e;
+  two_prod(a.hi, b.hi, p, e);
+  e = fma(a.hi, b.lo, e);
+  e = fma(a.lo, b.hi, e);
+  dd r;
+  fast_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+GBS_HD dd operator*(dd a, double b) {
+  double p, e;
+  two_prod(a.hi, b, p, e);
+  e = fma(a.lo, b, e);
+  dd r;
+  fast_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+GBS_HD dd operator+(dd a, double b) {
+  double s, e;
+  two_sum(a.hi, b, s, e);
+  e += a.lo;
+  dd r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+// x - a*b
+GBS_HD dd fms(dd x, dd a, dd b) { return x - a * b; }
+GBS_HD dd fpa(dd x, dd a, dd b) { return x + a * b; }
+GBS_HD double to_double(dd a) { return a.hi + a.lo; }
+
+// 1/sqrt(a) for a > 0: one Newton step x + x(1 - a x^2)/2 from the FP64 value
+// takes the ~52 correct bits of the start to ~104.
+__device__ __forceinline__ dd rsqrt_(dd a) {
+  double x0 = rsqrt(a.hi);
+  dd x = dd_make(x0);
+  dd r = dd_make(1.0) - a * (x * x);
+  return x + (x * r) * 0.5;
+}
+
+// ---------------------------------------------------------- triple-double --
+struct td {
+  double x0, x1, x2;
+};
+GBS_HD td td_make(double a) { return td{a, 0.0, 0.0}; }
+GBS_HD td operator-(td a) { return td{-a.x0, -a.x1, -a.x2}; }
+
+// Exact re-packing of a value given as the sum of four roughly decreasing
+// doubles into three: two bottom-up TwoSum sweeps (each one exact), then the
+// fourth word is folded into the third (error ~2^-53 of the third word).
+GBS_HD td td_renorm(double a, double b, double c, double d) {
+  two_sum(c, d, c, d);
+  two_sum(b, c, b, c);
+  two_sum(a, b, a, b);
+  two_sum(c, d, c, d);
+  two_sum(b, c, b, c);
+  two_sum(a, b, a, b);
+  two_sum(b, c + d, b, c);
+  return td{a, b, c};
+}
+GBS_HD td operator+(td a, td b) {
+  double s0, e0, s1, e1, s2, e2;
+  two_sum(a.x0, b.x0, s0, e0);
+  two_sum(a.x1, b.x1, s1, e1);
+  two_sum(a.x2, b.x2, s2, e2);
+  double t1, f1;
+  two_sum(e0, s1, t1, f1);
+  double t2, f2;
+  two_sum(f1, e1, t2, f2);
+  two_sum(t2, s2, t2, e1);
+  return td_renorm(s0, t1, t2, f2 + e1 + e2);
+}
+GBS_HD td operator-(td a, td b) { return a + (-b); }
+GBS_HD td operator*(td a, td b) {
+  double p0, q0, p1, q1, p2, q2;
+  two_prod(a.x0, b.x0, p0, q0);  // weight 1
+  two_prod(a.x0, b.x1, p1, q1);  // weight 2^-53
+  two_prod(a.x1, b.x0, p2, q2);  // weight 2^-53
+  double t3 = fma(a.x0, b.x2, fma(a.x1, b.x1, a.x2 * b.x0));  // weight 2^-106
+  double s1, e1, e2;
+  two_sum(p1, p2, s1, e1);
+  two_sum(s1, q0, s1, e2);
+  double s2, e3;
+  two_sum(e1, e2, s2, e3);
+  double s3 = (q1 + q2) + t3;
+  double u2, e4;
+  two_sum(s2, s3, u2, e4);
+  return td_renorm(p0, s1, u2, e3 + e4 + fma(a.x1, b.x2, a.x2 * b.x1));
+}
+GBS_HD td operator*(td a, double b) {
+  double p0, q0, p1, q1;
+  two_prod(a.x0, b, p0, q0);
+  two_prod(a.x1, b, p1, q1);
+  double s1, e1;
+  two_sum(p1, q0, s1, e1);
+  double s2, e2;
+  two_sum(e1, q1, s2, e2);
+  return td_renorm(p0, s1, s2, fma(a.x2, b, e2));
+}
+GBS_HD td operator+(td a, double b) { return a + td_make(b); }
+GBS_HD td fms(td x, td a, td b) { return x - a * b; }
+GBS_HD td fpa(td x, td a, td b) { return x + a * b; }
+GBS_HD double to_double(td a) { return a.x0 + (a.x1 + a.x2); }
+__device__ __forceinline__ td rsqrt_(td a) {
+  // Two Newton steps: 52 -> 104 -> ~159 bits.
+  td x = td_make(rsqrt(a.x0));
+  for (int it = 0; it < 2; ++it) {
+    td r = td_make(1.0) - a * (x * x);
+    x = x + (x * r) * 0.5;
+  }
+  return x;
+}
+
+// -------------------------------------------------------- plain types -----
+GBS_HD double fms(double x, double a, double b) { return fma(-a, b, x); }
+GBS_HD double fpa(double x, double a, double b) { return fma(a, b, x); }
+GBS_HD float fms(float x, float a, float b) { return fmaf(-a, b, x); }
+GBS_HD float fpa(float x, float a, float b) { return fmaf(a, b, x); }
+GBS_HD double to_double(double a) { return a; }
+GBS_HD double to_double(float a) { return (double)a; }
+__device__ __forceinline__ double rsqrt_(double a) { return rsqrt(a); }
+__device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
+
+template <class T> GBS_HD T from_double(double a);
+template <> GBS_HD double from_double<double>(double a) { return a; }
+template <> GBS_HD float from_double<float>(double a) { return (float)a; }
+template <> GBS_HD dd from_double<dd>(double a) { return dd_make(a); }
+template <> GBS_HD td from_double<td>(double a) { return td_make(a); }
+
+// ----------------------------------------------------------- complex ------
+template <class T>
+struct cplx {
+  T re, im;
+};
+
+// Entry types of the tree: T (real symmetric) or cplx<T> (complex Hermitian).
+// The functions below give both the same interface.
+template <class T> GBS_HD T re_of(const T& x) { return x; }
+template <class T> GBS_HD T re_of(const cplx<T>& x) { return x.re; }
+
+// |x|^2
+template <class T> GBS_HD T norm2(const T& x) { return x * x; }
+template <class T> GBS_HD T norm2(const cplx<T>& x) { return fpa(x.re * x.re, x.im, x.im); }
+
+// x - a * conj(b)
+template <class T> GBS_HD T fms_conj(const T& x, const T& a, const T& b) { return fms(x, a, b); }
+template <class T> GBS_HD cplx<T> fms_conj(const cplx<T>& x, const cplx<T>& a, const cplx<T>& b) {
+  cplx<T> r;
+  r.re = fms(fms(x.re, a.re, b.re), a.im, b.im);
+  r.im = fpa(fms(x.im, a.im, b.re), a.re, b.im);
+  return r;
+}
+// Re(x - a * conj(b)) as a real entry (diagonal of a Hermitian update)
+template <class T> GBS_HD T fms_conj_re(const T& x, const T& a, const T& b) { return fms(x, a, b); }
+template <class T> GBS_HD cplx<T> fms_conj_re(const cplx<T>& x, const cplx<T>& a, const cplx<T>& b) {
+  cplx<T> r;
+  r.re = fms(fms(x.re, a.re, b.re), a.im, b.im);
+  r.im = from_double<T>(0.0);
+  return r;
+}
+// a * s (s real) + b * w (w general):  used for L = u P^-1
+template <class T> GBS_HD T lin2(const T& a, const T& s, const T& b, const T& w) { return fpa(a * s, b, w); }
+template <class T>
+GBS_HD cplx<T> lin2(const cplx<T>& a, const T& s, const cplx<T>& b, const cplx<T>& w) {
+  cplx<T> r;
+  r.re = fms(fpa(a.re * s, b.re, w.re), b.im, w.im);
+  r.im = fpa(fpa(a.im * s, b.re, w.im), b.im, w.re);
+  return r;
+}
+template <class T> GBS_HD T conj_(const T& x) { return x; }
+template <class T> GBS_HD cplx<T> conj_(const cplx<T>& x) { return cplx<T>{x.re, -x.im}; }
+template <class T> GBS_HD T neg_(const T& x) { return -x; }
+template <class T> GBS_HD cplx<T> neg_(const cplx<T>& x) { return cplx<T>{-x.re, -x.im}; }
+
+template <class E> struct real_of { typedef E type; };
+template <class T> struct real_of<cplx<T>> { typedef T type; };
+
+template <class E> struct is_cplx { static const bool value = false; };
+template <class T> struct is_cplx<cplx<T>> { static const bool value = true; };
+
+}  // namespace gbs

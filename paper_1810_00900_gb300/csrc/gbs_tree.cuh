@@ -1,0 +1,285 @@
+// Subset-determinant decision tree (the hot path).
+//
+// For a 2n x 2n Hermitian (complex basis) or symmetric (real x/p basis)
+// positive-definite matrix G, whose rows 2i, 2i+1 belong to mode i, the tree
+// enumerates all 2^n mode subsets Z and the terms det(G_Z)^(-1/2), summed as
+//   f_inc = sum over Z containing the last mode  of (-1)^(n-|Z|) det(G_Z)^(-1/2)
+//   f_exc = sum over Z without the last mode     of (-1)^(n-|Z|) det(G_Z)^(-1/2)
+//   abs   = sum over all Z of det(G_Z)^(-1/2)
+// With G = (Sigma^-1)_S this gives the Torontonian Tor(O_S) = f_inc + f_exc;
+// with G a conditioned Sigma' over S u {k} (k last) it gives both sums of the
+// chain-rule sampler's no-click probability.  Every term is one of the paper's
+// vacuum probabilities (Eq. 5), and the signed sums are its click/no-click
+// bookkeeping (Eqs. 6-7) in closed form.
+//
+// Tree: decide the modes in order.  A node with q undecided modes holds C, the
+// Schur complement of those modes given the included ones, and s, the product
+// of det(P)^(-1/2) over the included pivots P, so that at a leaf
+// s = det(G_Z)^(-1/2) (block elimination: det [[P, B], [B^H, D]] = det P *
+// det(D - B^H P^-1 B), the identity behind the paper's Eq. 4a).  Excluding the
+// first undecided mode drops its two rows; including it replaces C by
+// C - C[:, p] P^-1 C[p, :] (a rank-2 update) and s by s det(P)^(-1/2).
+//
+// Work split:
+//   levels 0 .. n-Q-1   breadth first, one kernel per level, one thread per
+//                       (node, row of the child); node matrices live in global
+//                       memory as packed lower triangles, entry-major (SoA).
+//   last Q levels       one thread per node: a depth-first subtree unrolled at
+//                       compile time with every matrix in registers; all 32
+//                       lanes of a warp run the identical instruction stream on
+//                       different nodes (the tree is perfectly regular).
+//   reduction           per-block partials in the accumulation type, then one
+//                       block sums them in a fixed order (bitwise deterministic).
+#pragma once
+#include "gbs_num.cuh"
+
+namespace gbs {
+
+constexpr int sym(int d) { return d * (d + 1) / 2; }
+GBS_HD constexpr int tri(int a, int b) { return a * (a + 1) / 2 + b; }  // b <= a
+
+template <class E, class T>
+GBS_HD E scale_(const E& x, const T& s);
+template <>
+GBS_HD double scale_<double, double>(const double& x, const double& s) { return x * s; }
+template <>
+GBS_HD float scale_<float, float>(const float& x, const float& s) { return x * s; }
+template <>
+GBS_HD dd scale_<dd, dd>(const dd& x, const dd& s) { return x * s; }
+template <>
+GBS_HD td scale_<td, td>(const td& x, const td& s) { return x * s; }
+template <>
+GBS_HD cplx<double> scale_<cplx<double>, double>(const cplx<double>& x, const double& s) { return {x.re * s, x.im * s}; }
+template <>
+GBS_HD cplx<float> scale_<cplx<float>, float>(const cplx<float>& x, const float& s) { return {x.re * s, x.im * s}; }
+template <>
+GBS_HD cplx<dd> scale_<cplx<dd>, dd>(const cplx<dd>& x, const dd& s) { return {x.re * s, x.im * s}; }
+template <>
+GBS_HD cplx<td> scale_<cplx<td>, td>(const cplx<td>& x, const td& s) { return {x.re * s, x.im * s}; }
+
+// ------------------------------------------------ accumulation types -----
+// Per-thread accumulators (Acc) and cross-thread reduction values (Red).
+template <class T> struct acc_traits;
+template <> struct acc_traits<double> { typedef double Acc; typedef dd Red; };
+template <> struct acc_traits<float> { typedef double Acc; typedef dd Red; };
+template <> struct acc_traits<dd> { typedef dd Acc; typedef dd Red; };
+template <> struct acc_traits<td> { typedef td Acc; typedef td Red; };
+
+GBS_HD void acc_add(double& a, double x) { a += x; }
+GBS_HD void acc_add(double& a, float x) { a += (double)x; }
+GBS_HD void acc_add(dd& a, const dd& x) { a = a + x; }
+GBS_HD void acc_add(td& a, const td& x) { a = a + x; }
+GBS_HD void acc_sub(double& a, double x) { a -= x; }
+GBS_HD void acc_sub(double& a, float x) { a -= (double)x; }
+GBS_HD void acc_sub(dd& a, const dd& x) { a = a - x; }
+GBS_HD void acc_sub(td& a, const td& x) { a = a - x; }
+
+GBS_HD dd to_red(double a, dd*) { return dd_make(a); }
+GBS_HD dd to_red(const dd& a, dd*) { return a; }
+GBS_HD td to_red(const td& a, td*) { return a; }
+GBS_HD dd red_add(const dd& a, const dd& b) { return a + b; }
+GBS_HD td red_add(const td& a, const td& b) { return a + b; }
+GBS_HD dd red_neg(const dd& a) { return -a; }
+GBS_HD td red_neg(const td& a) { return -a; }
+GBS_HD void red_store(const dd& a, double* o) { o[0] = a.hi; o[1] = a.lo; o[2] = 0.0; }
+GBS_HD void red_store(const td& a, double* o) { o[0] = a.x0; o[1] = a.x1; o[2] = a.x2; }
+template <class R> GBS_HD R red_zero();
+template <> GBS_HD dd red_zero<dd>() { return dd_make(0.0); }
+template <> GBS_HD td red_zero<td>() { return td_make(0.0); }
+
+__device__ __forceinline__ dd shfl_down(const dd& v, int off) {
+  return dd{__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off)};
+}
+__device__ __forceinline__ td shfl_down(const td& v, int off) {
+  return td{__shfl_down_sync(0xffffffffu, v.x0, off), __shfl_down_sync(0xffffffffu, v.x1, off),
+            __shfl_down_sync(0xffffffffu, v.x2, off)};
+}
+
+template <class Red>
+struct Partial {
+  Red inc, exc;
+  double abs;
+};
+
+// Result of one tree, as plain doubles: value = x[0] + x[1] + x[2].
+struct TreeOut {
+  double inc[3];
+  double exc[3];
+  double abs;
+};
+
+// ------------------------------------------------- device status codes ---
+enum : int { kStatusOk = 0, kStatusNotPD = 3 };
+
+// --------------------------------------------------- breadth-first level --
+// Parents: count nodes with q undecided modes, entry e of node i at par[e*count + i].
+// Children: 2*count nodes with q-1 modes; child 2i excludes the first mode of
+// node i, child 2i+1 includes it.
+template <class E>
+__global__ void tree_level_kernel(const E* __restrict__ par, const typename real_of<E>::type* __restrict__ spar,
+                                  long long count, int q, E* __restrict__ chi,
+                                  typename real_of<E>::type* __restrict__ schi, int* __restrict__ status) {
+  typedef typename real_of<E>::type T;
+  const int rows = 2 * q - 2;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= count * rows) return;
+  const long long node = tid % count;
+  const int a = (int)(tid / count);
+  const long long c2 = 2 * count;
+#define PAR(i, j) par[(long long)tri(i, j) * count + node]
+  const T p00 = re_of(PAR(0, 0));
+  const T p11 = re_of(PAR(1, 1));
+  const E p10 = PAR(1, 0);
+  const T det = p00 * p11 - norm2(p10);
+  if (!(to_double(det) > 0.0)) {
+    if (a == 0) atomicExch(status, (int)kStatusNotPD);
+    return;
+  }
+  const T g = rsqrt_(det);
+  const T inv = g * g;
+  const T q00 = p00 * inv, q11 = p11 * inv;
+  const E m10 = neg_(scale_(p10, inv));  // -p10 / det
+  const E u0 = PAR(a + 2, 0), u1 = PAR(a + 2, 1);
+  const E L0 = lin2(u0, q11, u1, m10);           // (u0 p11 - u1 p10) / det
+  const E L1 = lin2(u1, q00, u0, conj_(m10));    // (u1 p00 - u0 conj(p10)) / det
+  for (int b = 0; b < a; ++b) {
+    const E x = PAR(a + 2, b + 2);
+    E v = fms_conj(x, L0, PAR(b + 2, 0));
+    v = fms_conj(v, L1, PAR(b + 2, 1));
+    chi[(long long)tri(a, b) * c2 + 2 * node] = x;
+    chi[(long long)tri(a, b) * c2 + 2 * node + 1] = v;
+  }
+  {
+    const E x = PAR(a + 2, a + 2);
+    E v = fms_conj_re(x, L0, u0);
+    v = fms_conj_re(v, L1, u1);
+    chi[(long long)tri(a, a) * c2 + 2 * node] = x;
+    chi[(long long)tri(a, a) * c2 + 2 * node + 1] = v;
+  }
+  if (a == 0) {
+    const T s = spar[node];
+    schi[2 * node] = s;
+    schi[2 * node + 1] = s * g;
+  }
+#undef PAR
+}
+
+// ----------------------------------------------- register depth-first ----
+// Node with Q undecided modes whose matrix is the view c[tri(OFF + i, OFF + j)]
+// of an array of dimension D; NEG = odd number of exclusions above it.
+template <class E, int Q, int D, int OFF, bool NEG>
+struct Dfs {
+  typedef typename real_of<E>::type T;
+  typedef typename acc_traits<T>::Acc Acc;
+  static __device__ __forceinline__ void run(const E (&c)[sym(D)], const T& s, Acc& inc, Acc& exc, Acc& asum,
+                                             bool& bad) {
+    const T p00 = re_of(c[tri(OFF, OFF)]);
+    const T p11 = re_of(c[tri(OFF + 1, OFF + 1)]);
+    const E p10 = c[tri(OFF + 1, OFF)];
+    const T det = p00 * p11 - norm2(p10);
+    bad |= !(to_double(det) > 0.0);
+    const T g = rsqrt_(det);
+    if constexpr (Q == 1) {
+      const T sg = s * g;
+      // include leaf: sign (-1)^NEG; exclude leaf: one more exclusion
+      if (NEG) { acc_sub(inc, sg); acc_add(exc, s); } else { acc_add(inc, sg); acc_sub(exc, s); }
+      acc_add(asum, sg);
+      acc_add(asum, s);
+    } else {
+      constexpr int DN = 2 * Q - 2;
+      E cn[sym(DN)];
+      const T inv = g * g;
+      const T q00 = p00 * inv, q11 = p11 * inv;
+      const E m10 = neg_(scale_(p10, inv));
+#pragma unroll
+      for (int a = 0; a < DN; ++a) {
+        const E u0 = c[tri(OFF + 2 + a, OFF)], u1 = c[tri(OFF + 2 + a, OFF + 1)];
+        const E L0 = lin2(u0, q11, u1, m10);
+        const E L1 = lin2(u1, q00, u0, conj_(m10));
+#pragma unroll
+        for (int b = 0; b < a; ++b) {
+          E v = fms_conj(c[tri(OFF + 2 + a, OFF + 2 + b)], L0, c[tri(OFF + 2 + b, OFF)]);
+          cn[tri(a, b)] = fms_conj(v, L1, c[tri(OFF + 2 + b, OFF + 1)]);
+        }
+        E v = fms_conj_re(c[tri(OFF + 2 + a, OFF + 2 + a)], L0, u0);
+        cn[tri(a, a)] = fms_conj_re(v, L1, u1);
+      }
+      Dfs<E, Q - 1, DN, 0, NEG>::run(cn, s * g, inc, exc, asum, bad);
+      Dfs<E, Q - 1, D, OFF + 2, !NEG>::run(c, s, inc, exc, asum, bad);
+    }
+  }
+};
+
+template <class Red>
+__device__ __forceinline__ void block_reduce_store(Red inc, Red exc, double asum, Partial<Red>* out) {
+  __shared__ Red s_inc[32], s_exc[32];
+  __shared__ double s_abs[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    inc = red_add(inc, shfl_down(inc, off));
+    exc = red_add(exc, shfl_down(exc, off));
+    asum += __shfl_down_sync(0xffffffffu, asum, off);
+  }
+  if (lane == 0) { s_inc[warp] = inc; s_exc[warp] = exc; s_abs[warp] = asum; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    Red a = s_inc[0], b = s_exc[0];
+    double c = s_abs[0];
+    for (int w = 1; w < nw; ++w) { a = red_add(a, s_inc[w]); b = red_add(b, s_exc[w]); c += s_abs[w]; }
+    out->inc = a; out->exc = b; out->abs = c;
+  }
+}
+
+// One thread per node with Q undecided modes; depth = n - Q levels above.
+template <class E, int Q>
+__global__ void __launch_bounds__(128) tree_leaf_kernel(const E* __restrict__ nodes,
+                                                        const typename real_of<E>::type* __restrict__ snode,
+                                                        long long count, int depth,
+                                                        Partial<typename acc_traits<typename real_of<E>::type>::Red>* partials,
+                                                        int* __restrict__ status) {
+  typedef typename real_of<E>::type T;
+  typedef typename acc_traits<T>::Acc Acc;
+  typedef typename acc_traits<T>::Red Red;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  Red inc = red_zero<Red>(), exc = red_zero<Red>();
+  double asum = 0.0;
+  if (node < count) {
+    E c[sym(2 * Q)];
+#pragma unroll
+    for (int e = 0; e < sym(2 * Q); ++e) c[e] = nodes[(long long)e * count + node];
+    const T s = snode[node];
+    Acc ai = from_double<Acc>(0.0), ae = from_double<Acc>(0.0), aa = from_double<Acc>(0.0);
+    bool bad = false;
+    Dfs<E, Q, 2 * Q, 0, false>::run(c, s, ai, ae, aa, bad);
+    if (bad) atomicExch(status, (int)kStatusNotPD);
+    inc = to_red(ai, (Red*)nullptr);
+    exc = to_red(ae, (Red*)nullptr);
+    asum = to_double(aa);
+    // sign of the node: (-1)^(exclusions above) = (-1)^(depth - popcount(node))
+    if ((depth - __popcll((unsigned long long)node)) & 1) { inc = red_neg(inc); exc = red_neg(exc); }
+  }
+  block_reduce_store(inc, exc, asum, partials + blockIdx.x);
+}
+
+template <class Red>
+__global__ void tree_final_kernel(const Partial<Red>* __restrict__ partials, int nparts, TreeOut* out) {
+  Red inc = red_zero<Red>(), exc = red_zero<Red>();
+  double asum = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    inc = red_add(inc, partials[i].inc);
+    exc = red_add(exc, partials[i].exc);
+    asum += partials[i].abs;
+  }
+  __shared__ Partial<Red> res;
+  block_reduce_store(inc, exc, asum, &res);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    red_store(res.inc, out->inc);
+    red_store(res.exc, out->exc);
+    out->abs = res.abs;
+  }
+}
+
+}  // namespace gbs
