@@ -30,7 +30,8 @@
  *    is available from gbs_ctx_last_error().
  *  - Ownership: the caller owns every array it passes (host memory unless a
  *    parameter says "device"); the library copies what it keeps.  Handles
- *    (gbs_ctx, gbs_state) are owned by the caller and freed explicitly.
+ *    (gbs_ctx, gbs_state) are owned by the caller and freed explicitly; every
+ *    state must be freed before the context it was created on.
  *  - Thread safety: calls on one context are serialised internally; the
  *    request loop (gbs_submit / gbs_poll) may be used from any thread.
  */

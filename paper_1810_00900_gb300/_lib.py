@@ -9,6 +9,7 @@ from __future__ import annotations
 import ctypes
 import os
 import re
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -104,6 +105,8 @@ class Context:
         if st:
             raise GbsError(st, "gbs_ctx_create failed (device %d)" % device)
         self.h = h
+        # states must be freed before their context; close() frees the live ones
+        self._states = weakref.WeakSet()
 
     def check(self, st: int):
         if st:
@@ -111,6 +114,8 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
+            for st in list(self._states):
+                st.free()
             self.L.gbs_ctx_destroy(self.h)
             self.h = None
 
@@ -156,11 +161,13 @@ class Context:
 class State:
     def __init__(self, ctx: Context, h, M: int):
         self.ctx, self.h, self.M = ctx, h, M
+        ctx._states.add(self)
 
     def free(self):
-        if self.h:
+        # a state of a closed context was already freed by Context.close()
+        if self.h and getattr(self.ctx, "h", None):
             self.ctx.L.gbs_state_free(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -245,3 +252,4 @@ def subset_sum(ctx: Context, G, basis: str = "complex", prec: str = "fp64"):
     ctx.check(ctx.L.gbs_subset_sum(ctx.h, n, _p(G.view(np.float64)), BASIS[basis], PREC[prec], _p(inc), _p(exc),
                                    _p(tor), ctypes.byref(a)))
     return inc, exc, tor, a.value
+
