@@ -171,6 +171,40 @@ gbs_status gbs_torontonian(gbs_ctx* ctx, const gbs_state* st, const int* modes, 
 gbs_status gbs_subset_sum(gbs_ctx* ctx, int n, const double* G, int basis, int prec, double* inc, double* exc,
                           double* tor, double* abs_sum);
 
+/* ------------------------------------------------------- no allocation -- */
+
+/* Largest n accepted by gbs_subset_sum_static, and the size of the device
+ * array it works in. */
+#define GBS_STATIC_MAX_N 19
+#define GBS_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/* gbs_subset_sum for FP64, real basis, that allocates no memory at all.
+ * The paper has no counterpart; this exists for callers that cannot call
+ * cudaMalloc / cudaFree: cudaFree synchronises the whole device (fatal to a
+ * loop that overlaps work on several streams), memory owned by another
+ * allocator or a fixed pool must not be bypassed, and memory sized up front
+ * must not hit an allocation that can fail later.  The caller passes device
+ * buffers; the intermediate data (tree levels, partial sums, a status word)
+ * live in one file-scope __device__ array of GBS_STATIC_SCRATCH_BYTES, which
+ * every GPU that loads this library holds until the process exits.
+ *   G_dev   device, 2n x 2n real symmetric positive definite, row-major, mode i
+ *           on rows/columns 2i, 2i+1 (the lower triangle is read);
+ *   n       number of modes, 1 <= n <= GBS_STATIC_MAX_N (larger n: GBS_EINVAL,
+ *           nothing is launched);
+ *   out_dev device, 8 doubles: {tor_hi, tor_lo, inc_hi, inc_lo, exc_hi, exc_lo,
+ *           abs_sum, status}, with tor = inc + exc as in gbs_subset_sum and
+ *           status 0, or 3 (GBS_ENOTPD) when a pivot block was not positive
+ *           definite (then the sums are meaningless);
+ *   cuda_stream  the cudaStream_t the work is queued on (0 = legacy default).
+ * The call is asynchronous: it returns after queueing (GBS_OK), GBS_EINVAL or
+ * GBS_ECUDA (a launch failed, or the device array could not be located).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array and each leaves
+ * its data there: calls that can overlap on the GPU race and must be ordered
+ * by the caller (one stream, or events). */
+gbs_status gbs_subset_sum_static(const double* G_dev, int n, double* out_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

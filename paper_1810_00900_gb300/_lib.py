@@ -78,6 +78,7 @@ def load() -> ctypes.CDLL:
         "gbs_torontonian": (ctypes.c_int, [_vp, _vp, _ip, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, ctypes.POINTER(gbs_prob)]),
         "gbs_subset_sum": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]),
+        "gbs_subset_sum_static": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -253,3 +254,9 @@ def subset_sum(ctx: Context, G, basis: str = "complex", prec: str = "fp64"):
                                    _p(tor), ctypes.byref(a)))
     return inc, exc, tor, a.value
 
+
+def subset_sum_static(G_dev_ptr: int, n: int, out_dev_ptr: int, stream_ptr: int = 0) -> int:
+    """gbs_subset_sum_static on caller-owned device buffers (raw device addresses).
+    Queues the work on `stream_ptr` and returns the status code without waiting."""
+    L = load()
+    return int(L.gbs_subset_sum_static(_vp(G_dev_ptr), int(n), _vp(out_dev_ptr), _vp(stream_ptr)))

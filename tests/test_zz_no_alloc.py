@@ -1,0 +1,53 @@
+"""gbs_subset_sum_static, the entry point that allocates nothing, against gbs_subset_sum.
+
+Callers that cannot let a library call cudaMalloc / cudaFree (cudaFree stalls
+the whole device; their memory belongs to another allocator or a fixed pool)
+pass their own device buffers to gbs_subset_sum_static, which keeps its
+intermediate data in the library's static device array.  Here the caller's
+buffers come from PyTorch's allocator.  Two calls in a row (of different sizes)
+check that reusing the array, which still holds the previous call's data,
+changes nothing; the tolerance is the FP64 one of tests/test_gpu_tree.py.
+"""
+import numpy as np
+import pytest
+
+import gbs_inputs as gi
+import oracle
+import paper_1810_00900_gb300 as gbs
+from helpers import real_basis_block
+from paper_1810_00900_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+
+
+def real_block(N, seed):
+    st = gi.uniform_squeezed_state(120, 0.7, seed=seed, eta=0.8)
+    Sig = oracle.sigma(oracle.covariance(st.U, st.r, st.eta))
+    return real_basis_block(oracle.sigma_inv_block(Sig, gi.random_modes(120, N, seed=seed)))
+
+
+def test_static_entry_point_matches_allocating_entry_point():
+    import torch
+    from paper_1810_00900_gb300 import build
+    build.build()
+    ctx = gbs.Context(0)
+    stream = torch.cuda.Stream()
+    for n, seed in ((17, 1), (11, 5)):
+        G = real_block(n, seed)
+        inc, exc, tor, asum = gbs.subset_sum(ctx, G, "real", "fp64")
+        G_dev = torch.from_numpy(G).to("cuda")
+        out = torch.full((8,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        st = _lib.subset_sum_static(G_dev.data_ptr(), n, out.data_ptr(), stream.cuda_stream)
+        stream.synchronize()
+        assert st == 0
+        o = out.cpu().numpy()
+        assert o[7] == 0.0  # status: every pivot positive definite
+        tol = 8 * n * 2.0 ** -53 * asum
+        assert abs((o[0] + o[1]) - (tor[0] + tor[1])) <= tol
+        assert abs((o[2] + o[3]) - (inc[0] + inc[1])) <= tol
+        assert abs((o[4] + o[5]) - (exc[0] + exc[1])) <= tol
+        assert abs(o[6] - asum) <= 1e-12 * asum
+    # beyond the stated maximum: rejected before anything is queued
+    assert _lib.subset_sum_static(G_dev.data_ptr(), 20, out.data_ptr(), stream.cuda_stream) == _lib.EINVAL
+    ctx.close()
