@@ -196,6 +196,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=19, help="click count of the oracle's CPU sample")
     ap.add_argument("--ref-sample", type=int, default=16, help="click count per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default="", help="sub_e,d_top,grid_per_sm,level_threads (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -225,12 +227,22 @@ def main():
     modes = np.ascontiguousarray(modes24, dtype=np.int32)
     st = gbs.build_state(ctx, st_p.U, st_p.r, st_p.eta)
     complex_basis = args.basis == "complex"
+    if args.tuning:
+        se, dt, gr, lt = (int(x) for x in args.tuning.split(","))
+        ctx.set_tuning(args.prec, args.basis, se, dt, gr, lt)
+        tune_report = []
+    else:
+        tune_report = ctx.autotune(args.prec, args.basis, min(args.N, 22)) if not args.no_autotune else []
+    tuning = ctx.tuning(args.prec, args.basis)
     Q = {("fp64", False): 5, ("fp64", True): 4, ("dd", False): 4, ("dd", True): 3, ("td", False): 3,
          ("td", True): 2, ("fp32", False): 5, ("fp32", True): 4}[(args.prec, complex_basis)]
     Q = min(Q, args.N)
-    depth = args.N - Q
-    leaf_flops = (2 ** depth) * tree_flops(Q, complex_basis)
+    q_root = min(args.N, Q + tuning["sub_e"])
+    depth = args.N - q_root
+    leaf_flops = (2 ** depth) * tree_flops(q_root, complex_basis)
     total_flops = tree_flops(args.N, complex_basis)
+    kernel_name = ("batch_subtree_kernel (%d levels expanded in shared memory, then register depth-first %d levels)"
+                   % (q_root - Q, Q)) if tuning["sub_e"] else "batch_leaf_kernel (register depth-first, %d levels)" % Q
 
     # L2 flush buffer (larger than the 129 MB L2), written between timed steps.
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda:%d" % dev)
@@ -301,9 +313,10 @@ def main():
             "sum": "double-double" if args.prec in ("fp64", "dd", "fp32") else "triple-double",
             "l2": "flushed between steps (256 MB write); tree level buffers also exceed L2",
             "parallelism": "replicas" if ws > 1 else "single GPU",
+            "tuning": tuning, "autotune_candidates": len(tune_report),
         },
         "roofline": {
-            "bound": "alu", "kernel": "tree_leaf_kernel (register depth-first, last %d levels)" % Q,
+            "bound": "alu", "kernel": kernel_name,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "peak_source": "FP64 DFMA-chain kernel measured in this run (gbs_measure_fp64_peak)",
             "traffic": None, "flops_per_launch": leaf_flops, "leaf_ms_avg": leaf_avg_s * 1e3,

@@ -84,6 +84,7 @@ typedef struct {
   double logdet_sigma;   /* log det Sigma of the state */
   int prec_used;         /* gbs_prec that produced the value */
   int basis_used;        /* gbs_basis that produced the value */
+  int status;            /* GBS_OK, or GBS_ENOTPD for this request */
 } gbs_prob;
 
 /* ------------------------------------------------------------ context -- */
@@ -159,6 +160,38 @@ gbs_status gbs_sigma_inv_block(gbs_ctx* ctx, const gbs_state* st, const int* mod
  * holds the TD value), GBS_ENOMEM, GBS_ECUDA. */
 gbs_status gbs_torontonian(gbs_ctx* ctx, const gbs_state* st, const int* modes, int N, int prec, int basis,
                            double rel_tol, gbs_prob* out);
+
+/* Click probabilities of n_req requests in one batch: request i asks for the
+ * pattern modes[off_i .. off_i + N_per[i]) on states[i] (off_i = sum of the
+ * earlier N_per).  The requests may differ in state, M, N and loss; all their
+ * subset trees run together (one plan, one launch per tree level over the whole
+ * batch), and each result is bitwise the same as when evaluated alone.
+ * prec, basis, rel_tol as for gbs_torontonian (AUTO escalates per request).
+ * out: caller-owned array of n_req results; out[i].status flags GBS_ENOTPD per
+ * request.  Returns the first error; GBS_EPRECISION if some request stayed
+ * above rel_tol in TD (its result is still filled in). */
+gbs_status gbs_torontonian_batch(gbs_ctx* ctx, int n_req, const gbs_state* const* states, const int* modes,
+                                 const int* N_per, int prec, int basis, double rel_tol, gbs_prob* out);
+
+/* Launch shape of the batched enumeration, per (precision, basis):
+ *   sub_e          levels each subtree CTA (2^sub_e threads) expands in shared
+ *                  memory before its threads run the register depth-first
+ *                  leaves (0 = no in-CTA expansion, one thread per leaf root);
+ *   d_top          prefix depth the first kernel reaches by eliminating each
+ *                  node's included prefix modes in shared memory;
+ *   grid_per_sm    0 = one CTA per work unit; k > 0 = persistent grid of k CTAs
+ *                  per SM looping over the work units;
+ *   level_threads  target threads per breadth-first level launch (sets how
+ *                  many rows of a node one thread updates).
+ * gbs_autotune times candidate shapes on a synthetic n-mode tree (6 <= n <= 28)
+ * on the context stream and keeps the fastest for later calls; report (may be
+ * NULL) receives the timings as a JSON array, truncated to report_len bytes.
+ * The paper has no counterpart (its Titan runs used MPI + OpenMP, Sec. III). */
+gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, char* report, size_t report_len);
+gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub_e, int* d_top, int* grid_per_sm,
+                          long long* level_threads);
+gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_top, int grid_per_sm,
+                          long long level_threads);
 
 /* Signed subset sum of an explicit matrix, the enumeration alone:
  *   tor = sum over Z subset {0..n-1} of (-1)^(n-|Z|) det(G_Z)^(-1/2)

@@ -36,6 +36,7 @@ class gbs_prob(ctypes.Structure):
         ("p_hi", ctypes.c_double), ("p_lo", ctypes.c_double), ("tor", ctypes.c_double * 3),
         ("abs_sum", ctypes.c_double), ("kappa", ctypes.c_double), ("err_bound", ctypes.c_double),
         ("logdet_sigma", ctypes.c_double), ("prec_used", ctypes.c_int), ("basis_used", ctypes.c_int),
+        ("status", ctypes.c_int),
     ]
 
 
@@ -77,6 +78,14 @@ def load() -> ctypes.CDLL:
         "gbs_sigma_inv_block": (ctypes.c_int, [_vp, _vp, _ip, ctypes.c_int, ctypes.c_int, _dp]),
         "gbs_torontonian": (ctypes.c_int, [_vp, _vp, _ip, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, ctypes.POINTER(gbs_prob)]),
+        "gbs_torontonian_batch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), _ip, _ip, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_double, ctypes.POINTER(gbs_prob)]),
+        "gbs_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_char_p,
+                                        ctypes.c_size_t]),
+        "gbs_get_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _ip, _ip, _ip,
+                                          ctypes.POINTER(ctypes.c_longlong)]),
+        "gbs_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_longlong]),
         "gbs_subset_sum": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]),
         "gbs_subset_sum_static": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     }
@@ -151,6 +160,25 @@ class Context:
         g = ctypes.c_double()
         self.check(self.L.gbs_measure_fp64_peak(self.h, ctypes.byref(g)))
         return g.value
+
+    def autotune(self, prec: str = "fp64", basis: str = "real", n: int = 22):
+        """Time candidate launch shapes on an n-mode tree and keep the fastest; returns the timings."""
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        self.check(self.L.gbs_autotune(self.h, PREC[prec], BASIS[basis], int(n), buf, len(buf)))
+        return json.loads(buf.value.decode() or "[]")
+
+    def tuning(self, prec: str = "fp64", basis: str = "real") -> dict:
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        d = ctypes.c_longlong()
+        self.check(self.L.gbs_get_tuning(self.h, PREC[prec], BASIS[basis], ctypes.byref(a), ctypes.byref(b),
+                                         ctypes.byref(c), ctypes.byref(d)))
+        return {"sub_e": a.value, "d_top": b.value, "grid_per_sm": c.value, "level_threads": d.value}
+
+    def set_tuning(self, prec: str = "fp64", basis: str = "real", sub_e: int = 5, d_top: int = 10,
+                   grid_per_sm: int = 0, level_threads: int = 1 << 18):
+        self.check(self.L.gbs_set_tuning(self.h, PREC[prec], BASIS[basis], sub_e, d_top, grid_per_sm,
+                                         level_threads))
 
     def kernel_time(self):
         ms = ctypes.c_double()
@@ -241,6 +269,29 @@ def torontonian(ctx: Context, st: State, modes, prec: str = "auto", basis: str =
                                     float(rel_tol), ctypes.byref(out)))
     return Prob(out.p_hi, out.p_lo, tuple(out.tor), out.abs_sum, out.kappa, out.err_bound, out.logdet_sigma,
                 PREC_NAME[out.prec_used], BASIS_NAME[out.basis_used])
+
+
+def _prob(out: gbs_prob) -> "Prob":
+    return Prob(out.p_hi, out.p_lo, tuple(out.tor), out.abs_sum, out.kappa, out.err_bound, out.logdet_sigma,
+                PREC_NAME[out.prec_used], BASIS_NAME[out.basis_used])
+
+
+def torontonian_batch(ctx: Context, states, patterns, prec: str = "auto", basis: str = "auto",
+                      rel_tol: float = 0.0, check: bool = True):
+    """Click probabilities of many (state, pattern) requests in one batch."""
+    n = len(patterns)
+    if len(states) != n:
+        raise ValueError("one state per pattern")
+    hs = (_vp * max(n, 1))(*[s.h for s in states])
+    Ns = np.array([len(p) for p in patterns], dtype=np.int32)
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.int32) for p in patterns])
+                                if n and Ns.sum() else np.zeros(1, dtype=np.int32), dtype=np.int32)
+    outs = (gbs_prob * max(n, 1))()
+    st = ctx.L.gbs_torontonian_batch(ctx.h, n, hs, _i(flat), _i(Ns) if n else None, PREC[prec], BASIS[basis],
+                                     float(rel_tol), outs)
+    if check:
+        ctx.check(st)
+    return [_prob(outs[i]) for i in range(n)]
 
 
 def subset_sum(ctx: Context, G, basis: str = "complex", prec: str = "fp64"):

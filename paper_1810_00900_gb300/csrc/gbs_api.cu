@@ -58,85 +58,6 @@ gbs_status dev_reserve(gbs_ctx* ctx, DevBuf& b, size_t bytes) {
   return dev_alloc(ctx, b, bytes);
 }
 
-// p = Tor exp(-logdet/2), kappa, error model; Tor = inc + exc in triple-double.
-struct ProbOut {
-  double p_hi, p_lo;
-  double tor[3];
-  double abs_sum, kappa, err;
-  double inc[3], exc[3];
-  int status;
-};
-
-__global__ void finish_kernel(const TreeOut* __restrict__ t, const int* __restrict__ status, double logdet, double u,
-                              int n, ProbOut* __restrict__ out) {
-  if (threadIdx.x != 0) return;
-  const td a{t->inc[0], t->inc[1], t->inc[2]};
-  const td b{t->exc[0], t->exc[1], t->exc[2]};
-  const td tor = a + b;
-  const double sc = exp(-0.5 * logdet);
-  const td p = tor * sc;
-  out->p_hi = p.x0;
-  out->p_lo = p.x1 + p.x2;
-  out->tor[0] = tor.x0;
-  out->tor[1] = tor.x1;
-  out->tor[2] = tor.x2;
-  out->abs_sum = t->abs;
-  const double tv = tor.x0 + (tor.x1 + tor.x2);
-  out->kappa = tv != 0.0 ? t->abs / fabs(tv) : INFINITY;
-  out->err = 4.0 * (n > 0 ? n : 1) * u * t->abs * sc;
-  for (int i = 0; i < 3; ++i) {
-    out->inc[i] = t->inc[i];
-    out->exc[i] = t->exc[i];
-  }
-  out->status = *status;
-}
-
-static double unit_roundoff(int prec) {
-  switch (prec) {
-    case GBS_PREC_FP64: return ldexp(1.0, -53);
-    case GBS_PREC_DD: return ldexp(1.0, -102);
-    case GBS_PREC_TD: return ldexp(1.0, -152);
-    case GBS_PREC_FP32_DIAG: return ldexp(1.0, -24);
-  }
-  return 1.0;
-}
-
-static gbs_status run_variant(gbs_ctx* ctx, int prec, bool real, const void* G, int n, TreeOut* out) {
-  switch (prec) {
-    case GBS_PREC_FP64: return real ? tree_fp64_real(ctx, G, n, out) : tree_fp64_cplx(ctx, G, n, out);
-    case GBS_PREC_DD: return real ? tree_dd_real(ctx, G, n, out) : tree_dd_cplx(ctx, G, n, out);
-    case GBS_PREC_TD: return real ? tree_td_real(ctx, G, n, out) : tree_td_cplx(ctx, G, n, out);
-    case GBS_PREC_FP32_DIAG: return real ? tree_fp32_real(ctx, G, n, out) : tree_fp32_cplx(ctx, G, n, out);
-  }
-  return set_error(ctx, GBS_EINVAL, "unknown precision");
-}
-
-// Run the tree over the packed root already in ctx->hbuf (n modes) and read back.
-static gbs_status eval_tree(gbs_ctx* ctx, int prec, bool real, int n, double logdet, ProbOut* host) {
-  gbs_status st;
-  if ((st = dev_reserve(ctx, ctx->out, sizeof(TreeOut) + sizeof(ProbOut) + 64))) return st;
-  TreeOut* tout = (TreeOut*)ctx->out.ptr;
-  ProbOut* pout = (ProbOut*)((char*)ctx->out.ptr + ((sizeof(TreeOut) + 15) / 16) * 16);
-  if ((st = run_variant(ctx, prec, real, ctx->hbuf.ptr, n, tout))) return st;
-  finish_kernel<<<1, 32, 0, ctx->stream>>>(tout, (const int*)ctx->status.ptr, logdet, unit_roundoff(prec), n, pout);
-  count_launch(ctx);
-  if ((st = check_cuda(ctx, cudaGetLastError(), "finish"))) return st;
-  if ((st = check_cuda(ctx, cudaMemcpyAsync(ctx->host_out, pout, sizeof(ProbOut), cudaMemcpyDeviceToHost, ctx->stream),
-                       "readback")))
-    return st;
-  if ((st = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync"))) return st;
-  if (ctx->timing && ctx->leaf_timer.pending) {
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ctx->leaf_timer.start, ctx->leaf_timer.stop);
-    ctx->leaf_timer.total_ms += ms;
-    ctx->leaf_timer.count += 1;
-    ctx->leaf_timer.pending = false;
-  }
-  memcpy(host, ctx->host_out, sizeof(ProbOut));
-  if (host->status == kStatusNotPD) return set_error(ctx, GBS_ENOTPD, "a pivot block is not positive definite");
-  return GBS_OK;
-}
-
 static gbs_status validate_modes(gbs_ctx* ctx, const int* modes, int N, int M) {
   if (N < 0 || N > 32) return set_error(ctx, GBS_EINVAL, "N must be in [0, 32]");
   if (N > 0 && !modes) return set_error(ctx, GBS_EINVAL, "modes is NULL");
@@ -148,17 +69,9 @@ static gbs_status validate_modes(gbs_ctx* ctx, const int* modes, int N, int M) {
   return GBS_OK;
 }
 
-static void fill_prob(gbs_prob* out, const ProbOut& r, int prec, bool real, double logdet) {
-  out->p_hi = r.p_hi;
-  out->p_lo = r.p_lo;
-  for (int i = 0; i < 3; ++i) out->tor[i] = r.tor[i];
-  out->abs_sum = r.abs_sum;
-  out->kappa = r.kappa;
-  out->err_bound = r.err;
-  out->logdet_sigma = logdet;
-  out->prec_used = prec;
-  out->basis_used = real ? GBS_BASIS_REAL : GBS_BASIS_COMPLEX;
-}
+// gbs_batch_api.cu
+gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, const int* const* modes, const int* N,
+                       int prec, int basis, double rel_tol, gbs_prob* out);
 
 }  // namespace gbs
 
@@ -212,13 +125,14 @@ void gbs_ctx_destroy(gbs_ctx* ctx) {
   server_shutdown(ctx);
   cudaStreamSynchronize(ctx->stream);
   DevBuf* bufs[] = {&ctx->lvl[0], &ctx->lvl[1], &ctx->sbuf[0], &ctx->sbuf[1], &ctx->partials,
-                    &ctx->out,    &ctx->status, &ctx->hbuf};
+                    &ctx->out,    &ctx->status, &ctx->hbuf,    &ctx->stage_dev, &ctx->aux_dev};
   for (DevBuf* b : bufs) dev_free(ctx, *b);
   if (ctx->leaf_timer.start) {
     cudaEventDestroy(ctx->leaf_timer.start);
     cudaEventDestroy(ctx->leaf_timer.stop);
   }
   if (ctx->host_out) cudaFreeHost(ctx->host_out);
+  if (ctx->stage_host) cudaFreeHost(ctx->stage_host);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -329,39 +243,9 @@ gbs_status gbs_torontonian(gbs_ctx* ctx, const gbs_state* st, const int* modes, 
   gbs_status e;
   if ((e = validate_modes(ctx, modes, N, st->M))) return e;
   if (prec < GBS_PREC_AUTO || prec > GBS_PREC_FP32_DIAG) return set_error(ctx, GBS_EINVAL, "bad precision");
-  const bool real = basis != GBS_BASIS_COMPLEX;
-  const double logdet = st->logdet_sigma;
-  if (N == 0) {
-    // Only the empty subset: Tor = 1, p = vacuum probability of every mode.
-    memset(out, 0, sizeof *out);
-    const double p = exp(-0.5 * logdet);
-    out->p_hi = p;
-    out->tor[0] = 1.0;
-    out->abs_sum = 1.0;
-    out->kappa = 1.0;
-    out->logdet_sigma = logdet;
-    out->prec_used = prec == GBS_PREC_AUTO ? GBS_PREC_FP64 : prec;
-    out->basis_used = real ? GBS_BASIS_REAL : GBS_BASIS_COMPLEX;
-    return GBS_OK;
-  }
-  const int D = 2 * N, ne = D * (D + 1) / 2;
-  if ((e = dev_reserve(ctx, ctx->hbuf, ne * (real ? 8 : 16)))) return e;
-  if ((e = click_block(ctx, st, modes, N, real ? 1 : 0, ctx->hbuf.ptr))) return e;
-  const double tol = rel_tol > 0 ? rel_tol : 1e-10;
-  ProbOut r;
-  if (prec != GBS_PREC_AUTO) {
-    if ((e = eval_tree(ctx, prec, real, N, logdet, &r))) return e;
-    fill_prob(out, r, prec, real, logdet);
-    return GBS_OK;
-  }
-  const int ladder[3] = {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD};
-  for (int i = 0; i < 3; ++i) {
-    if ((e = eval_tree(ctx, ladder[i], real, N, logdet, &r))) return e;
-    fill_prob(out, r, ladder[i], real, logdet);
-    const double p = fabs(r.p_hi);
-    if (r.err <= tol * p) return GBS_OK;
-  }
-  return set_error(ctx, GBS_EPRECISION, "the triple-double error estimate exceeds rel_tol");
+  const int* mp[1] = {modes};
+  const int Nv[1] = {N};
+  return probs_batch(ctx, 1, &st, mp, Nv, prec, basis, rel_tol, out);
 }
 
 gbs_status gbs_subset_sum(gbs_ctx* ctx, int n, const double* G, int basis, int prec, double* inc, double* exc,
@@ -384,13 +268,14 @@ gbs_status gbs_subset_sum(gbs_ctx* ctx, int n, const double* G, int basis, int p
       }
     }
   gbs_status e;
-  if ((e = dev_reserve(ctx, ctx->hbuf, packed.size() * 8))) return e;
-  if ((e = check_cuda(ctx, cudaMemcpyAsync(ctx->hbuf.ptr, packed.data(), packed.size() * 8, cudaMemcpyHostToDevice,
-                                           ctx->stream),
-                      "copy G")))
-    return e;
+  if ((e = stage_begin(ctx, packed.size() * 8 + (1 << 16)))) return e;
+  const void* G_dev = nullptr;
+  if ((e = stage(ctx, packed.data(), packed.size() * 8, &G_dev))) return e;
+  const BatchTree tree{n, 0};
+  const double zero = 0.0;
   ProbOut r;
-  if ((e = eval_tree(ctx, prec, real, n, 0.0, &r))) return e;
+  if ((e = batch_eval(ctx, prec, real, 1, &tree, G_dev, &zero, &r))) return e;
+  if (r.status) return set_error(ctx, GBS_ENOTPD, "a pivot block is not positive definite");
   for (int i = 0; i < 3; ++i) {
     if (inc) inc[i] = r.inc[i];
     if (exc) exc[i] = r.exc[i];

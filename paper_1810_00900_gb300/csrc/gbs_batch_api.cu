@@ -1,0 +1,450 @@
+// Batched probabilities: staging arena, batched click blocks, per-tree finish,
+// the precision ladder over a batch, and gbs_torontonian_batch.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <set>
+#include <vector>
+
+#include "gbs_batch_driver.cuh"
+#include "gbs_internal.h"
+
+namespace gbs {
+
+gbs_status stage_begin(gbs_ctx* ctx, size_t bytes) {
+  bytes = (bytes + 4096 + 255) / 256 * 256;
+  if (bytes > ctx->stage_cap) {
+    gbs_status st;
+    if ((st = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync"))) return st;
+    size_t cap = std::max(bytes, ctx->stage_cap * 2);
+    cap = std::max(cap, (size_t)1 << 20);
+    if (ctx->stage_host) cudaFreeHost(ctx->stage_host);
+    ctx->stage_host = nullptr;
+    ctx->stage_cap = 0;
+    if ((st = check_cuda(ctx, cudaMallocHost(&ctx->stage_host, cap), "pinned staging"))) return st;
+    dev_free(ctx, ctx->stage_dev);
+    if ((st = dev_alloc(ctx, ctx->stage_dev, cap))) return st;
+    ctx->stage_cap = cap;
+  }
+  ctx->stage_off = 0;
+  return GBS_OK;
+}
+
+gbs_status stage(gbs_ctx* ctx, const void* data, size_t bytes, const void** dev) {
+  const size_t off = (ctx->stage_off + 255) / 256 * 256;
+  if (off + bytes > ctx->stage_cap) return set_error(ctx, GBS_ENOMEM, "staging arena too small for this call");
+  unsigned char* h = (unsigned char*)ctx->stage_host + off;
+  unsigned char* d = (unsigned char*)ctx->stage_dev.ptr + off;
+  if (bytes) memcpy(h, data, bytes);
+  ctx->stage_off = off + bytes;
+  *dev = d;
+  if (!bytes) return GBS_OK;
+  return check_cuda(ctx, cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, ctx->stream), "stage copy");
+}
+
+const BatchTune& batch_tune_for(gbs_ctx* ctx, int prec, bool real) {
+  return ctx->tune[prec < 0 || prec > 4 ? 1 : prec][real ? 1 : 0];
+}
+
+// ------------------------------------------------------- click blocks ---
+struct ClickReq {
+  const cplx<double>* U;      // factor form (or null)
+  const double* alpha;
+  const double* beta;
+  const cplx<double>* Sinv;   // dense form (when U is null)
+  long long pair_begin;
+  long long root_off;
+  int M, N;
+  ModeList S;
+};
+
+// One warp per (request, mode pair j >= k); writes the packed lower triangle.
+__global__ void batch_click_block_kernel(const ClickReq* __restrict__ reqs, int nreq, long long total_pairs,
+                                         int real_basis, void* __restrict__ roots) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= total_pairs) return;
+  int lo = 0, hi = nreq - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (reqs[mid].pair_begin <= w) lo = mid; else hi = mid - 1;
+  }
+  const ClickReq& q = reqs[lo];
+  const int p = (int)(w - q.pair_begin);
+  int j = 0;
+  while ((j + 1) * (j + 2) / 2 <= p) ++j;
+  const int k = p - j * (j + 1) / 2;
+  const int M = q.M;
+  double ar = 0, ai = 0, br = 0, bi = 0;  // A = (Sigma^-1)_{a_j a_k}, B = (Sigma^-1)_{a_j a^+_k}
+  cplx<double> h10{0, 0}, h11{0, 0};
+  if (q.U) {
+    const cplx<double>* uj = q.U + (long long)q.S.m[j] * M;
+    const cplx<double>* uk = q.U + (long long)q.S.m[k] * M;
+    for (int l = lane; l < M; l += 32) {
+      const cplx<double> x = uj[l], y = uk[l];
+      const double pr = x.re * y.re + x.im * y.im, pi = x.im * y.re - x.re * y.im;
+      const double qr = x.re * y.re - x.im * y.im, qi = x.re * y.im + x.im * y.re;
+      ar = fma(pr, q.alpha[l], ar);
+      ai = fma(pi, q.alpha[l], ai);
+      br = fma(qr, q.beta[l], br);
+      bi = fma(qi, q.beta[l], bi);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      ar += __shfl_down_sync(0xffffffffu, ar, off);
+      ai += __shfl_down_sync(0xffffffffu, ai, off);
+      br += __shfl_down_sync(0xffffffffu, br, off);
+      bi += __shfl_down_sync(0xffffffffu, bi, off);
+    }
+    h10 = {br, -bi};
+    h11 = {ar, -ai};
+  } else if (lane == 0) {
+    const long long D = 2LL * M;
+    const long long rj = q.S.m[j], rk = q.S.m[k];
+    const cplx<double> h00 = q.Sinv[rj * D + rk], h01 = q.Sinv[rj * D + rk + M];
+    h10 = q.Sinv[(rj + M) * D + rk];
+    h11 = q.Sinv[(rj + M) * D + rk + M];
+    ar = h00.re; ai = h00.im; br = h01.re; bi = h01.im;
+  }
+  if (lane != 0) return;
+  if (j == k) { ai = 0.0; h11.im = 0.0; }
+  const int a0 = 2 * j, b0 = 2 * k;
+  auto T3 = [](int a, int b) { return a * (a + 1) / 2 + b; };
+  if (real_basis) {
+    // q^+ h q with q = [[1, i], [1, -i]]/sqrt2, h = [[h00, h01], [h10, h11]]
+    double* o = (double*)roots + q.root_off;
+    o[T3(a0, b0)] = 0.5 * (ar + br + h10.re + h11.re);
+    o[T3(a0 + 1, b0)] = 0.5 * ((ai + bi) - (h10.im + h11.im));
+    o[T3(a0 + 1, b0 + 1)] = 0.5 * ((ar - br) - (h10.re - h11.re));
+    if (j != k) o[T3(a0, b0 + 1)] = -0.5 * (ai - bi + h10.im - h11.im);
+  } else {
+    cplx<double>* o = (cplx<double>*)roots + q.root_off;
+    o[T3(a0, b0)] = {ar, ai};
+    o[T3(a0 + 1, b0)] = h10;
+    o[T3(a0 + 1, b0 + 1)] = h11;
+    if (j != k) o[T3(a0, b0 + 1)] = {br, bi};
+  }
+}
+
+__global__ void batch_finish_kernel(const TreeOut* __restrict__ outs, const int* __restrict__ status,
+                                    const double* __restrict__ logdet, const int* __restrict__ nmodes, double u,
+                                    int ntrees, ProbOut* __restrict__ po) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntrees) return;
+  const TreeOut& o = outs[t];
+  const td a{o.inc[0], o.inc[1], o.inc[2]};
+  const td b{o.exc[0], o.exc[1], o.exc[2]};
+  const td tor = a + b;
+  const double sc = exp(-0.5 * logdet[t]);
+  const td p = tor * sc;
+  ProbOut r;
+  r.p_hi = p.x0;
+  r.p_lo = p.x1 + p.x2;
+  r.tor[0] = tor.x0; r.tor[1] = tor.x1; r.tor[2] = tor.x2;
+  r.abs_sum = o.abs;
+  const double tv = tor.x0 + (tor.x1 + tor.x2);
+  r.kappa = tv != 0.0 ? o.abs / fabs(tv) : INFINITY;
+  r.err = 4.0 * (nmodes[t] > 0 ? nmodes[t] : 1) * u * o.abs * sc;
+  for (int i = 0; i < 3; ++i) { r.inc[i] = o.inc[i]; r.exc[i] = o.exc[i]; }
+  r.status = status[t];
+  r.pad = 0;
+  po[t] = r;
+}
+
+static double unit_roundoff_b(int prec) {
+  switch (prec) {
+    case GBS_PREC_FP64: return ldexp(1.0, -53);
+    case GBS_PREC_DD: return ldexp(1.0, -102);
+    case GBS_PREC_TD: return ldexp(1.0, -152);
+    case GBS_PREC_FP32_DIAG: return ldexp(1.0, -24);
+  }
+  return 1.0;
+}
+
+static gbs_status batch_variant(gbs_ctx* ctx, int prec, bool real, int nt, const BatchTree* tr, const void* roots,
+                                TreeOut* outs, int* status) {
+  const BatchTune& tu = batch_tune_for(ctx, prec, real);
+  switch (prec) {
+    case GBS_PREC_FP64: return real ? batch_fp64_real(ctx, nt, tr, roots, outs, status, tu)
+                                    : batch_fp64_cplx(ctx, nt, tr, roots, outs, status, tu);
+    case GBS_PREC_DD: return real ? batch_dd_real(ctx, nt, tr, roots, outs, status, tu)
+                                  : batch_dd_cplx(ctx, nt, tr, roots, outs, status, tu);
+    case GBS_PREC_TD: return real ? batch_td_real(ctx, nt, tr, roots, outs, status, tu)
+                                  : batch_td_cplx(ctx, nt, tr, roots, outs, status, tu);
+    case GBS_PREC_FP32_DIAG: return real ? batch_fp32_real(ctx, nt, tr, roots, outs, status, tu)
+                                         : batch_fp32_cplx(ctx, nt, tr, roots, outs, status, tu);
+  }
+  return set_error(ctx, GBS_EINVAL, "unknown precision");
+}
+
+gbs_status batch_eval(gbs_ctx* ctx, int prec, bool real, int ntrees, const BatchTree* trees, const void* roots_dev,
+                      const double* logdet, ProbOut* host_out) {
+  if (ntrees <= 0) return GBS_OK;
+  gbs_status st;
+  const size_t n = (size_t)ntrees;
+  auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t bytes = r256(n * sizeof(TreeOut)) + r256(n * sizeof(ProbOut)) + r256(n * sizeof(int));
+  if ((st = dev_reserve(ctx, ctx->aux_dev, bytes))) return st;
+  unsigned char* base = (unsigned char*)ctx->aux_dev.ptr;
+  TreeOut* outs = (TreeOut*)base;
+  ProbOut* po = (ProbOut*)(base + ((n * sizeof(TreeOut) + 255) / 256) * 256);
+  int* status = (int*)((unsigned char*)po + ((n * sizeof(ProbOut) + 255) / 256) * 256);
+  std::vector<int> nm(n);
+  for (size_t t = 0; t < n; ++t) nm[t] = trees[t].n;
+  const void *d_logdet = nullptr, *d_n = nullptr;
+  if ((st = stage(ctx, logdet, n * sizeof(double), &d_logdet)) || (st = stage(ctx, nm.data(), n * sizeof(int), &d_n)))
+    return st;
+  if ((st = check_cuda(ctx, cudaMemsetAsync(status, 0, n * sizeof(int), ctx->stream), "memset"))) return st;
+  if ((st = batch_variant(ctx, prec, real, ntrees, trees, roots_dev, outs, status))) return st;
+  batch_finish_kernel<<<(ntrees + 127) / 128, 128, 0, ctx->stream>>>(
+      outs, status, (const double*)d_logdet, (const int*)d_n, unit_roundoff_b(prec), ntrees, po);
+  count_launch(ctx);
+  if ((st = check_cuda(ctx, cudaGetLastError(), "finish"))) return st;
+  if ((st = check_cuda(ctx, cudaMemcpyAsync(host_out, po, n * sizeof(ProbOut), cudaMemcpyDeviceToHost, ctx->stream),
+                       "readback")) ||
+      (st = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync")))
+    return st;
+  if (ctx->timing && ctx->leaf_timer.pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->leaf_timer.start, ctx->leaf_timer.stop);
+    ctx->leaf_timer.total_ms += ms;
+    ctx->leaf_timer.count += 1;
+    ctx->leaf_timer.pending = false;
+  }
+  return GBS_OK;
+}
+
+// Click blocks of several (state, modes) requests into ctx->hbuf; fills trees[].
+gbs_status batch_click_blocks(gbs_ctx* ctx, int nreq, const gbs_state* const* states, const int* const* modes,
+                              const int* N, bool real, std::vector<BatchTree>& trees) {
+  std::vector<ClickReq> reqs;
+  trees.resize(nreq);
+  long long pairs = 0, ent = 0;
+  for (int i = 0; i < nreq; ++i) {
+    ClickReq q{};
+    const gbs_state* st = states[i];
+    q.U = st->has_factors ? (const cplx<double>*)st->U.ptr : nullptr;
+    q.alpha = (const double*)st->alpha.ptr;
+    q.beta = (const double*)st->beta.ptr;
+    q.Sinv = (const cplx<double>*)st->Sinv.ptr;
+    q.M = st->M;
+    q.N = N[i];
+    for (int j = 0; j < 32; ++j) q.S.m[j] = j < N[i] ? modes[i][j] : 0;
+    q.pair_begin = pairs;
+    q.root_off = ent;
+    trees[i] = BatchTree{N[i], ent};
+    pairs += (long long)N[i] * (N[i] + 1) / 2;
+    ent += (long long)N[i] * (2 * N[i] + 1);  // sym(2N)
+    if (N[i] > 0) reqs.push_back(q);
+  }
+  gbs_status st;
+  if ((st = dev_reserve(ctx, ctx->hbuf, (size_t)std::max(1LL, ent) * (real ? 8 : 16)))) return st;
+  if (reqs.empty()) return GBS_OK;
+  const void* d = nullptr;
+  if ((st = stage(ctx, reqs.data(), reqs.size() * sizeof(ClickReq), &d))) return st;
+  const long long threads = pairs * 32;
+  batch_click_block_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(
+      (const ClickReq*)d, (int)reqs.size(), pairs, real ? 1 : 0, ctx->hbuf.ptr);
+  count_launch(ctx);
+  return check_cuda(ctx, cudaGetLastError(), "click blocks");
+}
+
+static void fill(gbs_prob* out, const ProbOut& r, int prec, bool real, double logdet) {
+  out->p_hi = r.p_hi;
+  out->p_lo = r.p_lo;
+  for (int i = 0; i < 3; ++i) out->tor[i] = r.tor[i];
+  out->abs_sum = r.abs_sum;
+  out->kappa = r.kappa;
+  out->err_bound = r.err;
+  out->logdet_sigma = logdet;
+  out->prec_used = prec;
+  out->basis_used = real ? GBS_BASIS_REAL : GBS_BASIS_COMPLEX;
+  out->status = r.status == kStatusNotPD ? GBS_ENOTPD : GBS_OK;
+}
+
+// Probabilities of a batch of requests with the precision ladder; out[] per request.
+gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, const int* const* modes, const int* N,
+                       int prec, int basis, double rel_tol, gbs_prob* out) {
+  const bool real = basis != GBS_BASIS_COMPLEX;
+  gbs_status st;
+  if ((st = stage_begin(ctx, (size_t)nreq * 8192 + (1 << 16)))) return st;
+  std::vector<BatchTree> trees;
+  if ((st = batch_click_blocks(ctx, nreq, states, modes, N, real, trees))) return st;
+  const double tol = rel_tol > 0 ? rel_tol : 1e-10;
+  // requests still to evaluate (N == 0 needs no tree: Tor = 1)
+  std::vector<int> todo;
+  for (int i = 0; i < nreq; ++i) {
+    if (N[i] == 0) {
+      memset(&out[i], 0, sizeof(gbs_prob));
+      out[i].p_hi = exp(-0.5 * states[i]->logdet_sigma);
+      out[i].tor[0] = 1.0;
+      out[i].abs_sum = 1.0;
+      out[i].kappa = 1.0;
+      out[i].logdet_sigma = states[i]->logdet_sigma;
+      out[i].prec_used = prec == GBS_PREC_AUTO ? GBS_PREC_FP64 : prec;
+      out[i].basis_used = real ? GBS_BASIS_REAL : GBS_BASIS_COMPLEX;
+    } else {
+      todo.push_back(i);
+    }
+  }
+  const int ladder[3] = {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD};
+  const int steps = prec == GBS_PREC_AUTO ? 3 : 1;
+  bool uncertified = false;
+  for (int k = 0; k < steps && !todo.empty(); ++k) {
+    const int pr = prec == GBS_PREC_AUTO ? ladder[k] : prec;
+    std::vector<BatchTree> sub(todo.size());
+    std::vector<double> ld(todo.size());
+    for (size_t i = 0; i < todo.size(); ++i) {
+      sub[i] = trees[todo[i]];
+      ld[i] = states[todo[i]]->logdet_sigma;
+    }
+    std::vector<ProbOut> res(todo.size());
+    if ((st = batch_eval(ctx, pr, real, (int)todo.size(), sub.data(), ctx->hbuf.ptr, ld.data(), res.data())))
+      return st;
+    std::vector<int> next;
+    for (size_t i = 0; i < todo.size(); ++i) {
+      fill(&out[todo[i]], res[i], pr, real, ld[i]);
+      if (prec == GBS_PREC_AUTO && res[i].status == 0 && !(res[i].err <= tol * fabs(res[i].p_hi)))
+        next.push_back(todo[i]);
+    }
+    todo.swap(next);
+    if (k == steps - 1 && !todo.empty()) uncertified = true;
+  }
+  for (int i = 0; i < nreq; ++i)
+    if (out[i].status) return set_error(ctx, out[i].status, "a pivot block is not positive definite");
+  if (uncertified) return set_error(ctx, GBS_EPRECISION, "the triple-double error estimate exceeds rel_tol");
+  return GBS_OK;
+}
+
+}  // namespace gbs
+
+using namespace gbs;
+
+extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, char* report, size_t report_len) {
+  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP32_DIAG || n < 6 || n > 28) return GBS_EINVAL;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  cudaSetDevice(ctx->device);
+  const bool real = basis != GBS_BASIS_COMPLEX;
+  // A synthetic well-conditioned positive-definite root (the timing does not
+  // depend on the values): identity plus a small symmetric perturbation.
+  const int D = 2 * n, ne = D * (D + 1) / 2;
+  std::vector<double> root(ne * (real ? 1 : 2), 0.0);
+  unsigned long long x = 0x9E3779B97F4A7C15ull;
+  for (int a = 0; a < D; ++a)
+    for (int b = 0; b <= a; ++b) {
+      const int t = a * (a + 1) / 2 + b;
+      x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+      const double v = (a == b) ? 1.0 : 0.02 * ((double)(x >> 11) * 0x1p-53 - 0.5);
+      if (real) root[t] = v; else { root[2 * t] = v; root[2 * t + 1] = (a == b) ? 0.0 : 0.5 * v; }
+    }
+  gbs_status st;
+  const BatchTree tree{n, 0};
+  const double zero = 0.0;
+  ProbOut out;
+  const BatchTune saved = ctx->tune[prec][real ? 1 : 0];
+  BatchTune best = saved;
+  double best_ms = 1e30;
+  std::string rep = "[";
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int subs[] = {0, 4, 5, 6};
+  const int tops[] = {6, 8, 10};
+  const int grids[] = {0, 8};
+  const long long lts[] = {1LL << 17, 1LL << 19};
+  for (int se : subs)
+    for (int dt : tops)
+      for (int gr : grids)
+        for (long long lt : lts) {
+          BatchTune cand;
+          cand.sub_e = se;
+          cand.d_top = dt;
+          cand.leaf_grid_per_sm = gr;
+          cand.level_threads = lt;
+          ctx->tune[prec][real ? 1 : 0] = cand;
+          float ms_best = 1e30f;
+          for (int rep_i = 0; rep_i < 3; ++rep_i) {
+            if ((st = stage_begin(ctx, root.size() * 8 + (1 << 16)))) goto done;
+            const void* d = nullptr;
+            if ((st = stage(ctx, root.data(), root.size() * 8, &d))) goto done;
+            cudaEventRecord(e0, ctx->stream);
+            if ((st = batch_eval(ctx, prec, real, 1, &tree, d, &zero, &out))) goto done;
+            cudaEventRecord(e1, ctx->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep_i > 0 && ms < ms_best) ms_best = ms;  // the first run warms up
+          }
+          char buf[160];
+          snprintf(buf, sizeof buf, "%s{\"sub_e\":%d,\"d_top\":%d,\"grid_per_sm\":%d,\"level_threads\":%lld,\"ms\":%.4f}",
+                   rep.size() > 1 ? "," : "", se, dt, gr, lt, ms_best);
+          rep += buf;
+          if (ms_best < best_ms) {
+            best_ms = ms_best;
+            best = cand;
+          }
+        }
+  st = GBS_OK;
+done:
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->tune[prec][real ? 1 : 0] = st == GBS_OK ? best : saved;
+  if (st == GBS_OK) ctx->tuned[prec][real ? 1 : 0] = true;
+  rep += "]";
+  if (report && report_len) {
+    snprintf(report, report_len, "%s", rep.c_str());
+  }
+  return st;
+}
+
+extern "C" gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub_e, int* d_top, int* grid_per_sm,
+                                     long long* level_threads) {
+  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP32_DIAG) return GBS_EINVAL;
+  const BatchTune& t = ctx->tune[prec][basis != GBS_BASIS_COMPLEX ? 1 : 0];
+  if (sub_e) *sub_e = t.sub_e;
+  if (d_top) *d_top = t.d_top;
+  if (grid_per_sm) *grid_per_sm = t.leaf_grid_per_sm;
+  if (level_threads) *level_threads = t.level_threads;
+  return GBS_OK;
+}
+
+extern "C" gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_top, int grid_per_sm,
+                                     long long level_threads) {
+  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP32_DIAG || sub_e < 0 || sub_e > 7 || d_top < 0 ||
+      d_top > 16 || grid_per_sm < 0 || level_threads < 1)
+    return GBS_EINVAL;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  BatchTune& t = ctx->tune[prec][basis != GBS_BASIS_COMPLEX ? 1 : 0];
+  t.sub_e = sub_e;
+  t.d_top = d_top;
+  t.leaf_grid_per_sm = grid_per_sm;
+  t.level_threads = level_threads;
+  return GBS_OK;
+}
+
+extern "C" gbs_status gbs_torontonian_batch(gbs_ctx* ctx, int n_req, const gbs_state* const* states,
+                                            const int* modes, const int* N_per, int prec, int basis, double rel_tol,
+                                            gbs_prob* out) {
+  if (!ctx || n_req < 0 || (n_req > 0 && (!states || !N_per || !out))) return GBS_EINVAL;
+  if (prec < GBS_PREC_AUTO || prec > GBS_PREC_FP32_DIAG) return GBS_EINVAL;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  cudaSetDevice(ctx->device);
+  std::vector<const int*> mp(n_req);
+  long long off = 0;
+  for (int i = 0; i < n_req; ++i) {
+    if (!states[i] || states[i]->ctx != ctx) return set_error(ctx, GBS_EINVAL, "state of another context");
+    if (N_per[i] < 0 || N_per[i] > 32) return set_error(ctx, GBS_EINVAL, "N must be in [0, 32]");
+    if (N_per[i] > 0 && !modes) return set_error(ctx, GBS_EINVAL, "modes is NULL");
+    mp[i] = modes ? modes + off : nullptr;
+    std::set<int> seen;
+    for (int j = 0; j < N_per[i]; ++j) {
+      const int m = mp[i][j];
+      if (m < 0 || m >= states[i]->M) return set_error(ctx, GBS_EINVAL, "mode out of range");
+      if (!seen.insert(m).second) return set_error(ctx, GBS_EINVAL, "repeated mode");
+    }
+    off += N_per[i];
+  }
+  if (n_req == 0) return GBS_OK;
+  return probs_batch(ctx, n_req, states, mp.data(), N_per, prec, basis, rel_tol, out);
+}

@@ -13,6 +13,21 @@ namespace gbs {
 
 struct TreeOut;
 
+// One tree of a batch: n modes, packed FP64 root starting at entry root_off.
+struct BatchTree {
+  int n;
+  long long root_off;
+};
+
+// Launch parameters of the batched engine (chosen by the autotuner).
+struct BatchTune {
+  int d_top = 10;                       // depth the top kernel reaches per tree (at most)
+  int top_threads = 256;                // CTA size of the top kernel
+  long long level_threads = 1LL << 18;  // target threads per breadth-first level launch
+  int leaf_grid_per_sm = 0;             // 0: one CTA per work unit; k > 0: persistent, k CTAs per SM
+  int sub_e = 5;                        // levels each subtree CTA expands in shared memory (0: plain leaf)
+};
+
 // Device memory obtained by the library, accounted against the context budget.
 struct DevBuf {
   void* ptr = nullptr;
@@ -39,6 +54,12 @@ struct gbs_ctx {
 
   // tree workspace (grown on demand)
   gbs::DevBuf lvl[2], sbuf[2], partials, out, status, hbuf;
+  // batched engine: small tables staged host -> device through a bump arena
+  // (pinned host + device, reset at the start of each synchronous call) and
+  // the per-tree results
+  gbs::DevBuf stage_dev, aux_dev;
+  void* stage_host = nullptr;
+  size_t stage_cap = 0, stage_off = 0;
   // host-pinned readback
   void* host_out = nullptr;
 
@@ -47,6 +68,10 @@ struct gbs_ctx {
   gbs::KernelTimer leaf_timer;
   std::atomic<long long> launches{0};
   int sm_count = 0;
+
+  // batched-engine launch parameters per (precision, basis): [prec][real]
+  gbs::BatchTune tune[5][2];
+  bool tuned[5][2] = {};
 
   // request loop (see gbs_server.cu)
   void* server = nullptr;
@@ -76,18 +101,38 @@ gbs_status dev_reserve(gbs_ctx* ctx, DevBuf& b, size_t bytes);  // grow-only
 void dev_free(gbs_ctx* ctx, DevBuf& b);
 inline void count_launch(gbs_ctx* ctx, long long n = 1) { ctx->launches += n; }
 
-// Tree drivers (tree_*.cu).  G: packed lower-triangular root matrix on the
-// device (2n x 2n, entry tri(a, b) at index tri(a, b)), element type matching
-// the variant (double, double2 = complex, dd, ...), already mode-interleaved.
-// Results land in the device TreeOut *out and are NOT synchronised.
-gbs_status tree_fp64_real(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
-gbs_status tree_fp64_cplx(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
-gbs_status tree_dd_real(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
-gbs_status tree_dd_cplx(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
-gbs_status tree_td_real(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
-gbs_status tree_td_cplx(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
-gbs_status tree_fp32_real(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
-gbs_status tree_fp32_cplx(gbs_ctx* ctx, const void* G, int n, TreeOut* out);
+// Staging arena: stage_begin() makes room for `bytes` (synchronising first if it
+// must grow) and resets it; stage() copies host data into the next region and
+// queues the host -> device copy on the context stream.  (gbs_batch_api.cu)
+gbs_status stage_begin(gbs_ctx* ctx, size_t bytes);
+gbs_status stage(gbs_ctx* ctx, const void* data, size_t bytes, const void** dev);
+
+// Per-tree result after the finishing kernel (device and host layout).
+struct ProbOut {
+  double p_hi, p_lo;
+  double tor[3];
+  double abs_sum, kappa, err;
+  double inc[3], exc[3];
+  int status;
+  int pad;
+};
+
+gbs_status batch_fp64_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
+gbs_status batch_fp64_cplx(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
+gbs_status batch_dd_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
+gbs_status batch_dd_cplx(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
+gbs_status batch_td_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
+gbs_status batch_td_cplx(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
+gbs_status batch_fp32_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
+gbs_status batch_fp32_cplx(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
+
+// Evaluate ntrees trees whose packed FP64 roots are already in roots_dev
+// (entries at trees[t].root_off); logdet[t] (host) scales p = Tor exp(-logdet/2).
+// Synchronous: fills host_out[0..ntrees).  (gbs_batch_api.cu)
+gbs_status batch_eval(gbs_ctx* ctx, int prec, bool real, int ntrees, const BatchTree* trees, const void* roots_dev,
+                      const double* logdet, ProbOut* host_out);
+// The tuning in force for (prec, basis) -- the autotuner's choice when one was made.
+const BatchTune& batch_tune_for(gbs_ctx* ctx, int prec, bool real);
 
 // Up to 32 click modes passed by value as a kernel argument.
 struct ModeList {

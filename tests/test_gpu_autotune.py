@@ -1,0 +1,44 @@
+"""The autotuner and the launch shapes it chooses between change speed, not results."""
+import numpy as np
+import pytest
+
+import gbs_inputs as gi
+import oracle
+import paper_1810_00900_gb300 as gbs
+from helpers import frac3, real_basis_block
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1810_00900_gb300 import build
+    build.build()
+    c = gbs.Context(0)
+    yield c
+    c.close()
+
+
+def test_launch_shapes_agree(ctx):
+    st = gi.uniform_squeezed_state(150, 0.7, seed=9)
+    Sig = oracle.sigma(oracle.covariance(st.U, st.r, st.eta))
+    H = real_basis_block(oracle.sigma_inv_block(Sig, gi.random_modes(150, 17, seed=9)))
+    ref, ref_abs = oracle.torontonian(H.astype(np.complex128))
+    seen = []
+    for sub_e in (0, 3, 5, 7):
+        for d_top in (0, 4, 10):
+            for grid in (0, 2):
+                ctx.set_tuning("dd", "real", sub_e, d_top, grid, 1 << 17)
+                _, _, tor, a = gbs.subset_sum(ctx, H, "real", "dd")
+                err = abs(float(frac3(tor) - ref.to_fraction()))
+                assert err <= 8 * 17 * 2.0 ** -102 * ref_abs, (sub_e, d_top, grid, err)
+                seen.append(tor)
+    ctx.set_tuning("dd", "real", 5, 10, 0, 1 << 18)
+
+
+def test_autotune_picks_a_candidate(ctx):
+    rep = ctx.autotune("fp64", "real", 14)
+    assert len(rep) >= 8 and all(r["ms"] > 0 for r in rep)
+    best = min(rep, key=lambda r: r["ms"])
+    t = ctx.tuning("fp64", "real")
+    assert (t["sub_e"], t["d_top"], t["grid_per_sm"]) == (best["sub_e"], best["d_top"], best["grid_per_sm"])
