@@ -173,6 +173,47 @@ gbs_status gbs_torontonian(gbs_ctx* ctx, const gbs_state* st, const int* modes, 
 gbs_status gbs_torontonian_batch(gbs_ctx* ctx, int n_req, const gbs_state* const* states, const int* modes,
                                  const int* N_per, int prec, int basis, double rel_tol, gbs_prob* out);
 
+/* ------------------------------------------------------------ sampling -- */
+
+typedef struct {
+  long long steps;        /* no-click probabilities evaluated (one subset tree each) */
+  long long escalations;  /* trees repeated at a wider precision after the error check */
+  long long near_ties;    /* coin draws with |u - p0| < 1e-9 */
+  long long rejections;   /* trajectories abandoned by postselection (each may retry) */
+  double seconds;         /* wall time of the call */
+} gbs_sample_stats;
+
+/* Chain-rule threshold-detector samples (the paper's Sec. II algorithm in
+ * closed form).  Modes are measured from M-1 down to 0; at each step the
+ * probability p0 that the mode stays dark given the outcomes so far is one
+ * subset tree over the clicked modes plus the current one (on Sigma conditioned
+ * on the dark modes, Eq. 4a in Sigma form), and the mode stays dark iff
+ * u < p0 with u = (SplitMix64 output 1 + step + 2^20 (attempt + 2^12 sample) of
+ * the stream with state `seed`) >> 11 * 2^-53, where step = M-1-mode.
+ *   n_samples      number of samples (trajectories run together);
+ *   N_post         0: no postselection; > 0: keep only samples with exactly N_post
+ *                  clicks -- a trajectory is abandoned as soon as it has more, or
+ *                  can no longer reach N_post, and restarts with attempt + 1;
+ *   max_attempts   attempts per sample (>= 1); a sample that exhausts them is
+ *                  left as 0xFF in `patterns` and the call returns GBS_EREJECT;
+ *   forced_clicks  NULL, or n_samples x N_post click modes: the paper's forced-
+ *                  outcome benchmark (Sec. III B) -- the outcome of every step is
+ *                  preset (click iff the mode is listed) while p0 is still
+ *                  evaluated at every step;
+ *   prec           GBS_PREC_AUTO (per trajectory and step, the cheapest of FP64 /
+ *                  DD / TD keeping the estimated error of p0 below 1e-11) or a
+ *                  fixed GBS_PREC_FP64 / DD / TD;
+ *   patterns       caller-owned n_samples x M bytes (1 = click);
+ *   p0_out         NULL or caller-owned n_samples x M doubles, p0 of step s of
+ *                  sample i at [i * M + s] (last attempt);
+ *   stats          NULL or caller-owned.
+ * At most 31 clicks per trajectory (a free trajectory that exceeds it is treated
+ * as rejected).  Device memory: 32 M^2 bytes per sample for its conditioned
+ * Sigma.  Errors: GBS_EINVAL, GBS_EREJECT, GBS_ENOMEM, GBS_ENOTPD, GBS_ECUDA. */
+gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* st, int n_samples, uint64_t seed, int N_post, int max_attempts,
+                      const int* forced_clicks, int prec, uint8_t* patterns, double* p0_out,
+                      gbs_sample_stats* stats);
+
 /* Launch shape of the batched enumeration, per (precision, basis):
  *   sub_e          levels each subtree CTA (2^sub_e threads) expands in shared
  *                  memory before its threads run the register depth-first

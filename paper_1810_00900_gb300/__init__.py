@@ -7,5 +7,5 @@ Python binding; importing it does not touch the GPU.
 """
 from ._lib import (  # noqa: F401
     BASIS, PREC, Context, GbsError, Prob, State, build_state, header_functions, load, sigma_inv_block,
-    state_from_V, subset_sum, torontonian, torontonian_batch,
+    sample, state_from_V, subset_sum, torontonian, torontonian_batch,
 )

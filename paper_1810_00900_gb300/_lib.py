@@ -40,6 +40,11 @@ class gbs_prob(ctypes.Structure):
     ]
 
 
+class gbs_sample_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("escalations", ctypes.c_longlong),
+                ("near_ties", ctypes.c_longlong), ("rejections", ctypes.c_longlong), ("seconds", ctypes.c_double)]
+
+
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -86,6 +91,9 @@ def load() -> ctypes.CDLL:
                                           ctypes.POINTER(ctypes.c_longlong)]),
         "gbs_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_longlong]),
+        "gbs_sample": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _ip,
+                                      ctypes.c_int, ctypes.POINTER(ctypes.c_uint8), _dp,
+                                      ctypes.POINTER(gbs_sample_stats)]),
         "gbs_subset_sum": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]),
         "gbs_subset_sum_static": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     }
@@ -292,6 +300,26 @@ def torontonian_batch(ctx: Context, states, patterns, prec: str = "auto", basis:
     if check:
         ctx.check(st)
     return [_prob(outs[i]) for i in range(n)]
+
+
+def sample(ctx: Context, st: State, n_samples: int, seed: int, N_post: int = 0, max_attempts: int = 1,
+           forced_clicks=None, prec: str = "auto", want_p0: bool = False, check: bool = True):
+    """Chain-rule samples (gbs_sample): returns (patterns uint8 [n, M], p0 [n, M] or None, stats dict, status)."""
+    M = st.M
+    pats = np.zeros((n_samples, M), dtype=np.uint8)
+    p0 = np.zeros((n_samples, M)) if want_p0 else None
+    fc = None
+    if forced_clicks is not None:
+        fc = np.ascontiguousarray(forced_clicks, dtype=np.int32).reshape(n_samples, N_post)
+    stats = gbs_sample_stats()
+    status = ctx.L.gbs_sample(ctx.h, st.h, n_samples, ctypes.c_uint64(seed & ((1 << 64) - 1)), N_post, max_attempts,
+                              _i(fc) if fc is not None else None, PREC[prec],
+                              pats.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _p(p0) if want_p0 else None,
+                              ctypes.byref(stats))
+    if check and status not in (0, EREJECT):
+        ctx.check(status)
+    sd = {f: getattr(stats, f) for f, _ in gbs_sample_stats._fields_}
+    return pats, p0, sd, status
 
 
 def subset_sum(ctx: Context, G, basis: str = "complex", prec: str = "fp64"):

@@ -188,7 +188,7 @@ void gbs_state_free(gbs_state* st) {
   gbs_ctx* ctx = st->ctx;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
-  DevBuf* bufs[] = {&st->U, &st->r, &st->alpha, &st->beta, &st->V, &st->Sinv};
+  DevBuf* bufs[] = {&st->U, &st->r, &st->alpha, &st->beta, &st->V, &st->Sinv, &st->sig_real};
   for (DevBuf* b : bufs) dev_free(ctx, *b);
   delete st;
 }

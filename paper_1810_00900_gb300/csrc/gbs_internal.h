@@ -89,6 +89,7 @@ struct gbs_state {
   gbs::DevBuf beta;   // M doubles: (1/d+ - 1/d-)/2
   gbs::DevBuf V;      // 2M x 2M complex covariance, block order (a, a^+)
   gbs::DevBuf Sinv;   // 2M x 2M complex Sigma^-1 (states given by V only)
+  gbs::DevBuf sig_real;  // 2M x 2M Sigma in the real x/p basis (built by the first gbs_sample)
 };
 
 namespace gbs {

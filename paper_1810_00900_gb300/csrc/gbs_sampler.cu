@@ -1,0 +1,474 @@
+// Chain-rule click sampler (the paper's Sec. II update rule, in closed form).
+//
+// Modes are measured from the last to the first.  Each trajectory keeps its
+// own Sigma' = Sigma conditioned on vacuum at every mode that stayed dark so
+// far, in the real x/p basis, on the device.  At step k, with clicks S so far:
+//
+//   D  = sum_{W subset S} (-1)^|W| det(Sigma'_W)^(-1/2)
+//   Nn = sum_{W subset S} (-1)^|W| det(Sigma'_{W u k})^(-1/2)
+//   p0 = Nn / D   (probability that mode k stays dark)
+//
+// Both sums come from one subset tree over S u {k} with k last (the batched
+// engine): in its sign convention F_inc = (-1)^m Nn and F_exc = (-1)^(m+1) D,
+// so p0 = -F_inc / F_exc.  A device kernel draws u from SplitMix64 (output
+// 1 + step + 2^20 (attempt + 2^12 sample) of the stream with state `seed`),
+// keeps the mode dark iff u < p0 (or applies the forced outcome), and a dark
+// mode is conditioned away by the Schur complement
+//   Sigma' <- Sigma'_AA - Sigma'_Ak Sigma'_kk^-1 Sigma'_kA
+// (the paper's Eq. 4a in Sigma form), a rank-2 update of the active block.
+//
+// Precision: the cancellation ratio grows ~6x per click, so each trajectory's
+// tree runs in the cheapest of FP64 / double-double / triple-double whose
+// error estimate keeps |delta p0| below 1e-11, predicted from its previous
+// step and verified (escalated) after the fact.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gbs_internal.h"
+#include "gbs_num.cuh"
+#include "gbs_tree.cuh"
+
+namespace gbs {
+
+namespace {
+
+constexpr int kMaxClicks = 31;  // tree size m + 1 <= 32
+
+// Sigma = V + I/2 (complex, block order) -> real x/p basis, full 2M x 2M.
+__global__ void sigma_real_kernel(const cplx<double>* __restrict__ V, int M, double* __restrict__ S) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)M * M) return;
+  const int j = (int)(t / M), k = (int)(t % M);
+  const long long D = 2LL * M;
+  cplx<double> h00 = V[j * D + k], h01 = V[j * D + k + M];
+  cplx<double> h10 = V[(j + M) * D + k], h11 = V[(j + M) * D + k + M];
+  if (j == k) {
+    h00.re += 0.5;
+    h11.re += 0.5;
+  }
+  // q^+ h q with q = [[1, i], [1, -i]]/sqrt2 (columns x, p)
+  const long long r0 = 2LL * j, c0 = 2LL * k;
+  S[r0 * D + c0] = 0.5 * (h00.re + h01.re + h10.re + h11.re);
+  S[(r0 + 1) * D + c0] = 0.5 * ((h00.im + h01.im) - (h10.im + h11.im));
+  S[(r0 + 1) * D + c0 + 1] = 0.5 * ((h00.re - h01.re) - (h10.re - h11.re));
+  S[r0 * D + c0 + 1] = -0.5 * (h00.im - h01.im + h10.im - h11.im);
+}
+
+struct Traj {
+  double* sig;       // this trajectory's Sigma' (2M x 2M, full, row-major)
+  int* clicks;       // device list of clicked modes (capacity kMaxClicks + 1)
+  int m;             // clicks so far
+  int sample;        // sample index (RNG stream)
+  int attempt;
+  int tree;          // index of its tree in this step's batch (-1: idle)
+  long long root_off;
+};
+
+struct GatherItem {
+  const double* sig;
+  const int* clicks;
+  long long root_off;
+  int m, k, M, pad;
+};
+
+// root = Sigma'[S u {k}] (k last), packed lower triangle, one block per item.
+__global__ void gather_kernel(const GatherItem* __restrict__ items, double* __restrict__ roots) {
+  const GatherItem it = items[blockIdx.x];
+  const int n = it.m + 1, d = 2 * n;
+  const long long D = 2LL * it.M;
+  for (int e = threadIdx.x; e < d * (d + 1) / 2; e += blockDim.x) {
+    int a = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+    while (a * (a + 1) / 2 > e) --a;
+    while ((a + 1) * (a + 2) / 2 <= e) ++a;
+    const int b = e - a * (a + 1) / 2;
+    const int ma = (a >> 1) < it.m ? it.clicks[a >> 1] : it.k;
+    const int mb = (b >> 1) < it.m ? it.clicks[b >> 1] : it.k;
+    roots[it.root_off + e] = it.sig[(2LL * ma + (a & 1)) * D + 2LL * mb + (b & 1)];
+  }
+}
+
+struct DecideItem {
+  double inc[3], exc[3];  // tree sums of this step (final precision)
+  double* sig;            // Sigma' of the trajectory
+  int* clicks;
+  double* pinv;           // out: scaled inverse of the 2x2 pivot block (3 values)
+  int m, k, step, sample, attempt, forced, pad0, pad1;
+};
+
+struct DecideOut {
+  double p0;
+  int click, near_tie;
+};
+
+__device__ __forceinline__ double splitmix_u(unsigned long long seed, unsigned long long n) {
+  unsigned long long z = seed + n * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1p-53;
+}
+
+__global__ void decide_kernel(const DecideItem* __restrict__ items, int nitems, unsigned long long seed, int M,
+                              DecideOut* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nitems) return;
+  const DecideItem it = items[i];
+  // p0 = -inc / exc in triple-double: q = a/b by two correction steps
+  const td a{-it.inc[0], -it.inc[1], -it.inc[2]};
+  const td b{it.exc[0], it.exc[1], it.exc[2]};
+  const double q0 = a.x0 / b.x0;
+  const td r1 = a - b * q0;
+  const double q1 = r1.x0 / b.x0;
+  const td r2 = r1 - b * q1;
+  const double q2 = r2.x0 / b.x0;
+  const double p0 = q0 + (q1 + q2);
+  int click;
+  int near = 0;
+  if (it.forced >= 0) {
+    click = it.forced;
+  } else {
+    const unsigned long long n =
+        1ull + (unsigned long long)it.step +
+        (1ull << 20) * ((unsigned long long)it.attempt + (1ull << 12) * (unsigned long long)it.sample);
+    const double u = splitmix_u(seed, n);
+    click = !(u < p0);
+    near = fabs(u - p0) < 1e-9;
+  }
+  out[i] = DecideOut{p0, click, near};
+  if (click) {
+    it.clicks[it.m] = it.k;
+  } else {
+    // pivot block P = Sigma'[k, k] (2 x 2), its inverse for the conditioning
+    const long long D = 2LL * M;
+    const long long r = 2LL * it.k;
+    const double p00 = it.sig[r * D + r], p10 = it.sig[(r + 1) * D + r], p11 = it.sig[(r + 1) * D + r + 1];
+    const double inv = 1.0 / (p00 * p11 - p10 * p10);
+    it.pinv[0] = p11 * inv;   // (P^-1)_00
+    it.pinv[1] = -p10 * inv;  // (P^-1)_10
+    it.pinv[2] = p00 * inv;   // (P^-1)_11
+  }
+}
+
+struct CondItem {
+  double* sig;
+  const int* clicks;
+  const double* pinv;
+  double* L;       // 2 x A scratch: L row i at L[2i], L[2i+1]
+  long long entry_begin;
+  int m, k, A, pad;  // A = 2k + 2m active rows
+};
+
+__device__ __forceinline__ long long active_row(int i, int k, const int* clicks) {
+  return i < 2 * k ? (long long)i : 2LL * clicks[(i - 2 * k) >> 1] + ((i - 2 * k) & 1);
+}
+
+// L_i = Sigma'[i, k-block] P^-1 for every active row i.
+__global__ void cond_L_kernel(const CondItem* __restrict__ items, int M) {
+  const CondItem it = items[blockIdx.y];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= it.A) return;
+  const long long D = 2LL * M;
+  const long long ri = active_row(i, it.k, it.clicks);
+  const double u0 = it.sig[ri * D + 2LL * it.k], u1 = it.sig[ri * D + 2LL * it.k + 1];
+  it.L[2 * i] = fma(u0, it.pinv[0], u1 * it.pinv[1]);
+  it.L[2 * i + 1] = fma(u0, it.pinv[1], u1 * it.pinv[2]);
+}
+
+// Sigma'[i, j] -= L_i . Sigma'[k-block, j] over the active block.
+__global__ void cond_update_kernel(const CondItem* __restrict__ items, int nitems, long long total, int M) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int lo = 0, hi = nitems - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].entry_begin <= t) lo = mid; else hi = mid - 1;
+  }
+  const CondItem it = items[lo];
+  const long long e = t - it.entry_begin;
+  const int i = (int)(e / it.A), j = (int)(e % it.A);
+  const long long D = 2LL * M;
+  const long long ri = active_row(i, it.k, it.clicks), rj = active_row(j, it.k, it.clicks);
+  const double w0 = it.sig[(2LL * it.k) * D + rj], w1 = it.sig[(2LL * it.k + 1) * D + rj];
+  double* x = it.sig + ri * D + rj;
+  *x = fma(-it.L[2 * i], w0, fma(-it.L[2 * i + 1], w1, *x));
+}
+
+}  // namespace
+
+static gbs_status ensure_sigma_real(gbs_ctx* ctx, gbs_state* st) {
+  if (st->sig_real.ptr) return GBS_OK;
+  const long long M = st->M;
+  gbs_status e;
+  if ((e = dev_alloc(ctx, st->sig_real, (size_t)(4 * M * M) * sizeof(double)))) return e;
+  sigma_real_kernel<<<(unsigned)((M * M + 255) / 256), 256, 0, ctx->stream>>>((const cplx<double>*)st->V.ptr,
+                                                                              (int)M, (double*)st->sig_real.ptr);
+  count_launch(ctx);
+  return check_cuda(ctx, cudaGetLastError(), "sigma real");
+}
+
+static double unit_of(int prec) {
+  return prec == GBS_PREC_FP64 ? 0x1p-53 : prec == GBS_PREC_DD ? 0x1p-102 : 0x1p-152;
+}
+
+}  // namespace gbs
+
+using namespace gbs;
+
+extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_samples, uint64_t seed, int N_post,
+                                 int max_attempts, const int* forced_clicks, int prec, uint8_t* patterns,
+                                 double* p0_out, gbs_sample_stats* stats) {
+  if (!ctx || !cst || !patterns || n_samples < 1) return GBS_EINVAL;
+  if (N_post < 0 || N_post > kMaxClicks || (forced_clicks && N_post < 1)) return GBS_EINVAL;
+  if (prec != GBS_PREC_AUTO && prec != GBS_PREC_FP64 && prec != GBS_PREC_DD && prec != GBS_PREC_TD)
+    return GBS_EINVAL;
+  if (max_attempts < 1) max_attempts = 1;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  cudaSetDevice(ctx->device);
+  gbs_state* st = const_cast<gbs_state*>(cst);
+  const int M = st->M;
+  if (forced_clicks) {
+    for (long long i = 0; i < (long long)n_samples * N_post; ++i)
+      if (forced_clicks[i] < 0 || forced_clicks[i] >= M) return set_error(ctx, GBS_EINVAL, "forced click out of range");
+  }
+  const auto t_start = std::chrono::steady_clock::now();
+  gbs_status e;
+  if ((e = ensure_sigma_real(ctx, st))) return e;
+  const size_t sig_bytes = (size_t)4 * M * M * sizeof(double);
+  DevBuf work;
+  const int T = n_samples;
+  // per trajectory: Sigma', click list (64 ints), pivot inverse (4 doubles), L rows (2 x (2M + 64) doubles)
+  const size_t per_traj = sig_bytes + 64 * sizeof(int) + 4 * sizeof(double) + ((size_t)4 * M + 256) * sizeof(double);
+  if ((e = dev_alloc(ctx, work, per_traj * T + sizeof(DecideOut) * (size_t)T + 4096))) return e;
+  auto fail = [&](gbs_status code) {
+    dev_free(ctx, work);
+    return code;
+  };
+  unsigned char* base = (unsigned char*)work.ptr;
+  std::vector<Traj> tr(T);
+  std::vector<double*> pinv(T), Lbuf(T);
+  for (int t = 0; t < T; ++t) {
+    unsigned char* p = base + per_traj * t;
+    tr[t].sig = (double*)p;
+    tr[t].clicks = (int*)(p + sig_bytes);
+    pinv[t] = (double*)(p + sig_bytes + 64 * sizeof(int));
+    Lbuf[t] = pinv[t] + 4;
+    tr[t].sample = t;
+    tr[t].attempt = 0;
+  }
+  DecideOut* dout = (DecideOut*)(base + per_traj * T);
+  std::vector<std::vector<int>> S(T);
+  std::vector<int> status(T, 0);  // 0 running, 1 done, 2 rejected for good
+  std::vector<double> kappa_prev(T, 1.0);
+  std::vector<int> prec_prev(T, GBS_PREC_FP64);
+  std::vector<std::vector<char>> forced(T);
+  if (forced_clicks) {
+    for (int t = 0; t < T; ++t) {
+      forced[t].assign(M, 0);
+      for (int c = 0; c < N_post; ++c) forced[t][forced_clicks[(long long)t * N_post + c]] = 1;
+    }
+  }
+  gbs_sample_stats stt{};
+  memset(patterns, 0xFF, (size_t)T * M);
+  std::vector<int> wave(T);
+  for (int t = 0; t < T; ++t) wave[t] = t;
+  while (!wave.empty()) {
+    // (re)start the trajectories of this wave from the state
+    for (int t : wave) {
+      if ((e = check_cuda(ctx, cudaMemcpyAsync(tr[t].sig, st->sig_real.ptr, sig_bytes, cudaMemcpyDeviceToDevice,
+                                               ctx->stream),
+                          "init trajectory")))
+        return fail(e);
+      S[t].clear();
+      tr[t].m = 0;
+      kappa_prev[t] = 1.0;
+      prec_prev[t] = GBS_PREC_FP64;
+    }
+    std::vector<char> live(T, 0);
+    for (int t : wave) live[t] = 1;
+    for (int step = 0; step < M; ++step) {
+      const int k = M - 1 - step;
+      std::vector<int> act;
+      for (int t : wave)
+        if (live[t]) act.push_back(t);
+      if (act.empty()) break;
+      if ((e = stage_begin(ctx, act.size() * (sizeof(GatherItem) + sizeof(DecideItem) + sizeof(CondItem) + 16384) +
+                                    (1 << 16))))
+        return fail(e);
+      // ---- roots Sigma'[S u {k}]
+      std::vector<GatherItem> gi(act.size());
+      std::vector<BatchTree> trees(act.size());
+      long long ent = 0;
+      for (size_t i = 0; i < act.size(); ++i) {
+        const int t = act[i];
+        const int n = tr[t].m + 1;
+        gi[i] = GatherItem{tr[t].sig, tr[t].clicks, ent, tr[t].m, k, M, 0};
+        trees[i] = BatchTree{n, ent};
+        ent += (long long)n * (2 * n + 1);
+      }
+      if ((e = dev_reserve(ctx, ctx->hbuf, (size_t)ent * sizeof(double)))) return fail(e);
+      const void* dgi = nullptr;
+      if ((e = stage(ctx, gi.data(), gi.size() * sizeof(GatherItem), &dgi))) return fail(e);
+      gather_kernel<<<(unsigned)act.size(), 128, 0, ctx->stream>>>((const GatherItem*)dgi, (double*)ctx->hbuf.ptr);
+      count_launch(ctx);
+      // ---- trees, precision chosen per trajectory and verified
+      std::vector<ProbOut> res(act.size());
+      std::vector<int> used(act.size());
+      std::vector<int> want(act.size());
+      for (size_t i = 0; i < act.size(); ++i) {
+        const int t = act[i];
+        if (prec != GBS_PREC_AUTO) {
+          want[i] = prec;
+          continue;
+        }
+        // predicted kappa: the last one, times 8 per click since (margin)
+        const double kp = kappa_prev[t] * 8.0;
+        const double n = tr[t].m + 1;
+        const int ladder[3] = {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD};
+        want[i] = GBS_PREC_TD;
+        for (int l = 0; l < 3; ++l)
+          if (4.0 * n * unit_of(ladder[l]) * kp * 4.0 < 1e-11) {
+            want[i] = ladder[l];
+            break;
+          }
+        want[i] = std::max(want[i], prec_prev[t]);
+      }
+      std::vector<size_t> todo(act.size());
+      for (size_t i = 0; i < act.size(); ++i) todo[i] = i;
+      for (int round = 0; round < 3 && !todo.empty(); ++round) {
+        std::vector<size_t> next;
+        for (int pv : {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD}) {
+          std::vector<size_t> grp;
+          for (size_t i : todo)
+            if (want[i] == pv) grp.push_back(i);
+          if (grp.empty()) continue;
+          std::vector<BatchTree> sub(grp.size());
+          std::vector<double> zero(grp.size(), 0.0);
+          for (size_t j = 0; j < grp.size(); ++j) sub[j] = trees[grp[j]];
+          std::vector<ProbOut> r(grp.size());
+          if ((e = batch_eval(ctx, pv, true, (int)grp.size(), sub.data(), ctx->hbuf.ptr, zero.data(), r.data())))
+            return fail(e);
+          stt.steps += (long long)grp.size();
+          for (size_t j = 0; j < grp.size(); ++j) {
+            const size_t i = grp[j];
+            res[i] = r[j];
+            used[i] = pv;
+            if (r[j].status) return fail(set_error(ctx, GBS_ENOTPD, "sampler: a pivot block is not positive definite"));
+            const double exc = fabs(r[j].exc[0]), inc = fabs(r[j].inc[0]);
+            const double p0 = exc > 0 ? inc / exc : INFINITY;
+            const double n = trees[i].n;
+            const double dp = 4.0 * n * unit_of(pv) * r[j].abs_sum * (1.0 + p0) / std::max(exc, 1e-300);
+            if (prec == GBS_PREC_AUTO && !(dp < 1e-11) && pv != GBS_PREC_TD) {
+              want[i] = pv == GBS_PREC_FP64 ? GBS_PREC_DD : GBS_PREC_TD;
+              next.push_back(i);
+              stt.escalations++;
+            }
+          }
+        }
+        todo.swap(next);
+      }
+      // ---- decide on the device
+      std::vector<DecideItem> di(act.size());
+      for (size_t i = 0; i < act.size(); ++i) {
+        const int t = act[i];
+        DecideItem d{};
+        for (int c = 0; c < 3; ++c) {
+          d.inc[c] = res[i].inc[c];
+          d.exc[c] = res[i].exc[c];
+        }
+        d.sig = tr[t].sig;
+        d.clicks = tr[t].clicks;
+        d.pinv = pinv[t];
+        d.m = tr[t].m;
+        d.k = k;
+        d.step = step;
+        d.sample = tr[t].sample;
+        d.attempt = tr[t].attempt;
+        d.forced = forced_clicks ? (int)forced[t][k] : -1;
+        di[i] = d;
+        const double exc = fabs(res[i].exc[0]);
+        kappa_prev[t] = exc > 0 ? res[i].abs_sum / exc : 1e300;
+        prec_prev[t] = used[i];
+      }
+      const void* ddi = nullptr;
+      if ((e = stage(ctx, di.data(), di.size() * sizeof(DecideItem), &ddi))) return fail(e);
+      decide_kernel<<<(unsigned)((act.size() + 63) / 64), 64, 0, ctx->stream>>>((const DecideItem*)ddi,
+                                                                                (int)act.size(), seed, M, dout);
+      count_launch(ctx);
+      std::vector<DecideOut> dec(act.size());
+      if ((e = check_cuda(ctx, cudaMemcpyAsync(dec.data(), dout, act.size() * sizeof(DecideOut),
+                                               cudaMemcpyDeviceToHost, ctx->stream),
+                          "decide readback")) ||
+          (e = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync")))
+        return fail(e);
+      // ---- bookkeeping, postselection, conditioning of the dark modes
+      std::vector<CondItem> ci;
+      long long entries = 0;
+      for (size_t i = 0; i < act.size(); ++i) {
+        const int t = act[i];
+        if (p0_out) p0_out[(long long)tr[t].sample * M + step] = dec[i].p0;
+        stt.near_ties += dec[i].near_tie;
+        if (dec[i].click) {
+          S[t].push_back(k);
+          tr[t].m++;
+        }
+        const int mcount = tr[t].m;
+        bool reject = false;
+        if (N_post > 0 && !forced_clicks && (mcount > N_post || mcount + k < N_post)) reject = true;
+        if (!forced_clicks && mcount > kMaxClicks) reject = true;
+        if (reject) {
+          live[t] = 0;
+          status[t] = 2;
+          continue;
+        }
+        if (!dec[i].click && k > 0) {
+          const int A = 2 * k + 2 * mcount;
+          ci.push_back(CondItem{tr[t].sig, tr[t].clicks, pinv[t], Lbuf[t], entries, mcount, k, A, 0});
+          entries += (long long)A * A;
+        }
+        if (k == 0) {
+          live[t] = 0;
+          status[t] = 1;
+        }
+      }
+      if (!ci.empty()) {
+        const void* dci = nullptr;
+        if ((e = stage(ctx, ci.data(), ci.size() * sizeof(CondItem), &dci))) return fail(e);
+        int amax = 0;
+        for (const CondItem& c : ci) amax = std::max(amax, c.A);
+        dim3 gl((amax + 255) / 256, (unsigned)ci.size());
+        cond_L_kernel<<<gl, 256, 0, ctx->stream>>>((const CondItem*)dci, M);
+        cond_update_kernel<<<(unsigned)((entries + 255) / 256), 256, 0, ctx->stream>>>((const CondItem*)dci,
+                                                                                       (int)ci.size(), entries, M);
+        count_launch(ctx, 2);
+        if ((e = check_cuda(ctx, cudaGetLastError(), "conditioning"))) return fail(e);
+      }
+    }
+    // finished trajectories -> patterns; rejected ones retry with the next attempt
+    std::vector<int> next;
+    for (int t : wave) {
+      if (status[t] == 1) {
+        uint8_t* row = patterns + (size_t)tr[t].sample * M;
+        memset(row, 0, M);
+        for (int c : S[t]) row[c] = 1;
+      } else if (status[t] == 2) {
+        stt.rejections++;
+        if (tr[t].attempt + 1 < max_attempts) {
+          tr[t].attempt++;
+          status[t] = 0;
+          next.push_back(t);
+        }
+      }
+    }
+    wave.swap(next);
+  }
+  if ((e = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync"))) return fail(e);
+  dev_free(ctx, work);
+  stt.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  if (stats) *stats = stt;
+  for (int t = 0; t < T; ++t)
+    if (status[t] != 1) return set_error(ctx, GBS_EREJECT, "postselection attempts exhausted for some samples");
+  return GBS_OK;
+}
