@@ -156,6 +156,32 @@ def cpu_oracle_rate(n_sample: int):
     return (2 ** n_sample) / dt, dt, threads
 
 
+def sampler_block(ctx, gbs, gi, n_traj, ws, local):
+    """M = 800, r ~ U[0.3, 0.9], Haar seed 2, n_traj forced trajectories of 20 uniformly placed clicks
+    (the paper's forced-outcome benchmark); p0 is evaluated at all 800 steps of every trajectory."""
+    stp, clicks = gi.chain_sampling_workload(800, 20, n_traj, seed=2)
+    st = gbs.build_state(ctx, stp.U, stp.r, stp.eta)
+    ctx.autotune("dd", "real", 18)
+    ctx.autotune("td", "real", 18)
+    forced = np.array(clicks, dtype=np.int32)
+    gbs.sample(ctx, st, 2, seed=2, N_post=20, forced_clicks=forced[:2])  # warm-up
+    l0 = ctx.launch_count
+    barrier(ws)
+    t0 = time.perf_counter()
+    pats, p0, stats, status = gbs.sample(ctx, st, n_traj, seed=2, N_post=20, forced_clicks=forced, want_p0=True)
+    dt = allreduce_max(ws, time.perf_counter() - t0, local)
+    st.free()
+    return {"metric": "M=800,N=20 samples/s", "value": ws * n_traj / dt, "unit": "samples/s",
+            "seconds": dt, "trajectories": n_traj, "steps_evaluated": stats["steps"],
+            "escalations": stats["escalations"], "gpu_launches": ctx.launch_count - l0,
+            "trees_fp64_dd_td": stats["trees"], "tree_seconds_fp64_dd_td": stats["tree_seconds"],
+            "other_seconds": stats["cond_seconds"], "dd_tuning": ctx.tuning("dd", "real"),
+            "td_tuning": ctx.tuning("td", "real"),
+            "p0_range": [float(p0.min()), float(p0.max())], "status": status,
+            "workload": "M=800 modes, r~U[0.3,0.9], Haar seed 2, eta=1; %d forced trajectories with 20 uniform "
+                        "click positions; no-click probability at every one of the 800 steps" % n_traj}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -198,6 +224,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default="", help="sub_e,d_top,grid_per_sm,level_threads (skips the autotuner)")
+    ap.add_argument("--sampler-traj", type=int, default=64, help="forced trajectories of the M=800 sampler run (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -328,6 +355,8 @@ def main():
         "clocks": clk,
         "result": {"p": results[-1].p, "kappa": results[-1].kappa, "prec": results[-1].prec},
     }
+    if args.sampler_traj > 0:
+        line["sampler"] = sampler_block(ctx, gbs, gi, args.sampler_traj, ws, local)
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()

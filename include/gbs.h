@@ -181,6 +181,9 @@ typedef struct {
   long long near_ties;    /* coin draws with |u - p0| < 1e-9 */
   long long rejections;   /* trajectories abandoned by postselection (each may retry) */
   double seconds;         /* wall time of the call */
+  long long trees[3];     /* subset trees evaluated in FP64, DD, TD */
+  double tree_seconds[3]; /* wall time spent in those tree batches */
+  double cond_seconds;    /* wall time of gathers, decisions and conditioning */
 } gbs_sample_stats;
 
 /* Chain-rule threshold-detector samples (the paper's Sec. II algorithm in
@@ -215,9 +218,10 @@ gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* st, int n_samples, uint64_t
                       gbs_sample_stats* stats);
 
 /* Launch shape of the batched enumeration, per (precision, basis):
- *   sub_e          levels each subtree CTA (2^sub_e threads) expands in shared
- *                  memory before its threads run the register depth-first
- *                  leaves (0 = no in-CTA expansion, one thread per leaf root);
+ *   sub_e          0, or 5..7: levels each subtree CTA (2^sub_e threads, at
+ *                  least one warp) expands in shared memory before its threads
+ *                  run the register depth-first leaves (0 = no in-CTA
+ *                  expansion, one thread per leaf root);
  *   d_top          prefix depth the first kernel reaches by eliminating each
  *                  node's included prefix modes in shared memory;
  *   grid_per_sm    0 = one CTA per work unit; k > 0 = persistent grid of k CTAs

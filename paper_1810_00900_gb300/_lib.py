@@ -42,7 +42,9 @@ class gbs_prob(ctypes.Structure):
 
 class gbs_sample_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("escalations", ctypes.c_longlong),
-                ("near_ties", ctypes.c_longlong), ("rejections", ctypes.c_longlong), ("seconds", ctypes.c_double)]
+                ("near_ties", ctypes.c_longlong), ("rejections", ctypes.c_longlong), ("seconds", ctypes.c_double),
+                ("trees", ctypes.c_longlong * 3), ("tree_seconds", ctypes.c_double * 3),
+                ("cond_seconds", ctypes.c_double)]
 
 
 _lib = None
@@ -319,6 +321,8 @@ def sample(ctx: Context, st: State, n_samples: int, seed: int, N_post: int = 0, 
     if check and status not in (0, EREJECT):
         ctx.check(status)
     sd = {f: getattr(stats, f) for f, _ in gbs_sample_stats._fields_}
+    sd["trees"] = list(sd["trees"])
+    sd["tree_seconds"] = list(sd["tree_seconds"])
     return pats, p0, sd, status
 
 

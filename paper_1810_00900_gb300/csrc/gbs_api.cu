@@ -115,6 +115,18 @@ gbs_status gbs_ctx_create(gbs_ctx** out, int device, size_t hbm_budget_bytes) {
   }
   ctx->own_stream = true;
   cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  // Launch shapes before any autotuning: wider arithmetic makes the redundant
+  // prefix elimination of the top kernel dearer, so it stops earlier.
+  for (int b = 0; b < 2; ++b) {
+    ctx->tune[GBS_PREC_FP64][b].sub_e = 6;
+    ctx->tune[GBS_PREC_FP64][b].d_top = 8;
+    ctx->tune[GBS_PREC_FP32_DIAG][b].sub_e = 6;
+    ctx->tune[GBS_PREC_FP32_DIAG][b].d_top = 8;
+    ctx->tune[GBS_PREC_DD][b].sub_e = 6;
+    ctx->tune[GBS_PREC_DD][b].d_top = 5;
+    ctx->tune[GBS_PREC_TD][b].sub_e = 6;
+    ctx->tune[GBS_PREC_TD][b].d_top = 4;
+  }
   *out = ctx;
   return GBS_OK;
 }

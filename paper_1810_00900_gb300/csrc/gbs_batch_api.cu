@@ -349,7 +349,7 @@ extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, cha
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int subs[] = {0, 4, 5, 6};
+  const int subs[] = {0, 5, 6, 7};
   const int tops[] = {6, 8, 10};
   const int grids[] = {0, 8};
   const long long lts[] = {1LL << 17, 1LL << 19};
@@ -411,7 +411,8 @@ extern "C" gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub
 
 extern "C" gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_top, int grid_per_sm,
                                      long long level_threads) {
-  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP32_DIAG || sub_e < 0 || sub_e > 7 || d_top < 0 ||
+  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP32_DIAG || sub_e < 0 || sub_e > 7 ||
+      (sub_e > 0 && sub_e < 5) || d_top < 0 ||
       d_top > 16 || grid_per_sm < 0 || level_threads < 1)
     return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);

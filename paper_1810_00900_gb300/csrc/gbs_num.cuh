@@ -99,30 +99,23 @@ struct td {
 GBS_HD td td_make(double a) { return td{a, 0.0, 0.0}; }
 GBS_HD td operator-(td a) { return td{-a.x0, -a.x1, -a.x2}; }
 
-// Exact re-packing of a value given as the sum of four roughly decreasing
-// doubles into three: two bottom-up TwoSum sweeps (each one exact), then the
-// fourth word is folded into the third (error ~2^-53 of the third word).
-GBS_HD td td_renorm(double a, double b, double c, double d) {
-  two_sum(c, d, c, d);
-  two_sum(b, c, b, c);
-  two_sum(a, b, a, b);
-  two_sum(c, d, c, d);
-  two_sum(b, c, b, c);
-  two_sum(a, b, a, b);
-  two_sum(b, c + d, b, c);
-  return td{a, b, c};
+// Re-packing of x0 + x1 + x2 (roughly decreasing, possibly overlapping after
+// a cancellation) into three words: two exact TwoSum steps from the top.
+GBS_HD td td_pack(double x0, double x1, double x2) {
+  double a, b, c, d;
+  two_sum(x0, x1, a, b);
+  two_sum(b, x2, c, d);
+  return td{a, c, d};
 }
+// Sloppy triple-double addition: the error is bounded relative to the
+// operands (about 2^-155 max(|a|, |b|)), which is what the tree needs.
 GBS_HD td operator+(td a, td b) {
-  double s0, e0, s1, e1, s2, e2;
+  double s0, e0, s1, e1;
   two_sum(a.x0, b.x0, s0, e0);
   two_sum(a.x1, b.x1, s1, e1);
-  two_sum(a.x2, b.x2, s2, e2);
-  double t1, f1;
-  two_sum(e0, s1, t1, f1);
-  double t2, f2;
-  two_sum(f1, e1, t2, f2);
-  two_sum(t2, s2, t2, e1);
-  return td_renorm(s0, t1, t2, f2 + e1 + e2);
+  const double t2 = (a.x2 + b.x2) + e1;
+  two_sum(s1, e0, s1, e0);
+  return td_pack(s0, s1, t2 + e0);
 }
 GBS_HD td operator-(td a, td b) { return a + (-b); }
 GBS_HD td operator*(td a, td b) {
@@ -130,16 +123,11 @@ GBS_HD td operator*(td a, td b) {
   two_prod(a.x0, b.x0, p0, q0);  // weight 1
   two_prod(a.x0, b.x1, p1, q1);  // weight 2^-53
   two_prod(a.x1, b.x0, p2, q2);  // weight 2^-53
-  double t3 = fma(a.x0, b.x2, fma(a.x1, b.x1, a.x2 * b.x0));  // weight 2^-106
+  double t = fma(a.x0, b.x2, fma(a.x1, b.x1, a.x2 * b.x0)) + (q1 + q2);  // weight 2^-106
   double s1, e1, e2;
   two_sum(p1, p2, s1, e1);
   two_sum(s1, q0, s1, e2);
-  double s2, e3;
-  two_sum(e1, e2, s2, e3);
-  double s3 = (q1 + q2) + t3;
-  double u2, e4;
-  two_sum(s2, s3, u2, e4);
-  return td_renorm(p0, s1, u2, e3 + e4 + fma(a.x1, b.x2, a.x2 * b.x1));
+  return td_pack(p0, s1, t + (e1 + e2));
 }
 GBS_HD td operator*(td a, double b) {
   double p0, q0, p1, q1;
@@ -147,9 +135,7 @@ GBS_HD td operator*(td a, double b) {
   two_prod(a.x1, b, p1, q1);
   double s1, e1;
   two_sum(p1, q0, s1, e1);
-  double s2, e2;
-  two_sum(e1, q1, s2, e2);
-  return td_renorm(p0, s1, s2, fma(a.x2, b, e2));
+  return td_pack(p0, s1, fma(a.x2, b, q1) + e1);
 }
 GBS_HD td operator+(td a, double b) { return a + td_make(b); }
 GBS_HD td fms(td x, td a, td b) { return x - a * b; }

@@ -10,17 +10,24 @@
 //
 // Both sums come from one subset tree over S u {k} with k last (the batched
 // engine): in its sign convention F_inc = (-1)^m Nn and F_exc = (-1)^(m+1) D,
-// so p0 = -F_inc / F_exc.  A device kernel draws u from SplitMix64 (output
+// so p0 = -F_inc / F_exc.  After a dark step only half of that tree is new:
+// det Sigma'_{W u k} = det Sigma'_k det (Sigma'|k)_W gives
+//   Nn_k = det(Sigma'_k)^(-1/2) (-1)^m Tor_k,  Tor_k = tree over S of Sigma'|k,
+// and the next step's D is exactly (-1)^m Tor_k (conditioning on k is the same
+// Schur step), so a "half" step evaluates 2^m instead of 2^(m+1) terms.  The
+// full tree runs at the first step, after a click and when a step's error
+// check asks for a wider precision.  A device kernel draws u from SplitMix64 (output
 // 1 + step + 2^20 (attempt + 2^12 sample) of the stream with state `seed`),
 // keeps the mode dark iff u < p0 (or applies the forced outcome), and a dark
 // mode is conditioned away by the Schur complement
 //   Sigma' <- Sigma'_AA - Sigma'_Ak Sigma'_kk^-1 Sigma'_kA
 // (the paper's Eq. 4a in Sigma form), a rank-2 update of the active block.
 //
-// Precision: the cancellation ratio grows ~6x per click, so each trajectory's
-// tree runs in the cheapest of FP64 / double-double / triple-double whose
-// error estimate keeps |delta p0| below 1e-11, predicted from its previous
-// step and verified (escalated) after the fact.
+// Precision: the cancellation ratio grows with every click, so each
+// trajectory's tree runs in the cheapest of FP64 / double-double /
+// triple-double whose error bound keeps |delta p0| below 5e-10 (half the 1e-9
+// near-tie threshold), predicted from its previous step and verified
+// (escalated to a full tree at a wider precision) after the fact.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -70,15 +77,29 @@ struct Traj {
 struct GatherItem {
   const double* sig;
   const int* clicks;
+  double* s0;  // half mode: out, det(Sigma'_k)^(-1/2)
   long long root_off;
-  int m, k, M, pad;
+  int m, k, M, half;
 };
 
-// root = Sigma'[S u {k}] (k last), packed lower triangle, one block per item.
+// Full mode: root = Sigma'[S u {k}] (k last).  Half mode: root = (Sigma'|k)[S],
+// the Schur complement of mode k restricted to the clicked modes.  Packed lower
+// triangle, one block per item.
 __global__ void gather_kernel(const GatherItem* __restrict__ items, double* __restrict__ roots) {
   const GatherItem it = items[blockIdx.x];
-  const int n = it.m + 1, d = 2 * n;
+  const int n = it.half ? it.m : it.m + 1, d = 2 * n;
   const long long D = 2LL * it.M;
+  const long long rk = 2LL * it.k;
+  double q00 = 0, q10 = 0, q11 = 0;
+  if (it.half) {
+    const double p00 = it.sig[rk * D + rk], p10 = it.sig[(rk + 1) * D + rk], p11 = it.sig[(rk + 1) * D + rk + 1];
+    const double det = p00 * p11 - p10 * p10;
+    const double inv = 1.0 / det;
+    q00 = p11 * inv;
+    q10 = -p10 * inv;
+    q11 = p00 * inv;
+    if (threadIdx.x == 0) *it.s0 = rsqrt(det);
+  }
   for (int e = threadIdx.x; e < d * (d + 1) / 2; e += blockDim.x) {
     int a = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
     while (a * (a + 1) / 2 > e) --a;
@@ -86,16 +107,26 @@ __global__ void gather_kernel(const GatherItem* __restrict__ items, double* __re
     const int b = e - a * (a + 1) / 2;
     const int ma = (a >> 1) < it.m ? it.clicks[a >> 1] : it.k;
     const int mb = (b >> 1) < it.m ? it.clicks[b >> 1] : it.k;
-    roots[it.root_off + e] = it.sig[(2LL * ma + (a & 1)) * D + 2LL * mb + (b & 1)];
+    const long long ra = 2LL * ma + (a & 1), rb = 2LL * mb + (b & 1);
+    double x = it.sig[ra * D + rb];
+    if (it.half) {
+      const double ua0 = it.sig[ra * D + rk], ua1 = it.sig[ra * D + rk + 1];
+      const double ub0 = it.sig[rk * D + rb], ub1 = it.sig[(rk + 1) * D + rb];
+      const double l0 = fma(ua0, q00, ua1 * q10), l1 = fma(ua0, q10, ua1 * q11);
+      x = fma(-l0, ub0, fma(-l1, ub1, x));
+    }
+    roots[it.root_off + e] = x;
   }
 }
 
 struct DecideItem {
-  double inc[3], exc[3];  // tree sums of this step (final precision)
+  double inc[3], exc[3];  // full: tree sums; half: inc = Tor_k over S, exc unused
   double* sig;            // Sigma' of the trajectory
   int* clicks;
   double* pinv;           // out: scaled inverse of the 2x2 pivot block (3 values)
-  int m, k, step, sample, attempt, forced, pad0, pad1;
+  double* dcarry;         // in (half) / out: D of the next step, triple-double
+  const double* s0;       // half: det(Sigma'_k)^(-1/2)
+  int m, k, step, sample, attempt, forced, half, pad1;
 };
 
 struct DecideOut {
@@ -116,9 +147,18 @@ __global__ void decide_kernel(const DecideItem* __restrict__ items, int nitems, 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nitems) return;
   const DecideItem it = items[i];
-  // p0 = -inc / exc in triple-double: q = a/b by two correction steps
-  const td a{-it.inc[0], -it.inc[1], -it.inc[2]};
-  const td b{it.exc[0], it.exc[1], it.exc[2]};
+  const double sgn = (it.m & 1) ? -1.0 : 1.0;  // (-1)^m
+  // Nn (a) and D (b) in triple-double, then p0 = a/b by two correction steps
+  td a, b, xnext;
+  if (it.half) {
+    const td tor{it.inc[0], it.inc[1], it.inc[2]};
+    xnext = tor * sgn;  // (-1)^m Tor_k: D of the next step if k stays dark
+    a = xnext * (*it.s0);
+    b = td{it.dcarry[0], it.dcarry[1], it.dcarry[2]};
+  } else {
+    a = td{it.inc[0], it.inc[1], it.inc[2]} * sgn;
+    b = td{it.exc[0], it.exc[1], it.exc[2]} * (-sgn);
+  }
   const double q0 = a.x0 / b.x0;
   const td r1 = a - b * q0;
   const double q1 = r1.x0 / b.x0;
@@ -145,10 +185,16 @@ __global__ void decide_kernel(const DecideItem* __restrict__ items, int nitems, 
     const long long D = 2LL * M;
     const long long r = 2LL * it.k;
     const double p00 = it.sig[r * D + r], p10 = it.sig[(r + 1) * D + r], p11 = it.sig[(r + 1) * D + r + 1];
-    const double inv = 1.0 / (p00 * p11 - p10 * p10);
+    const double det = p00 * p11 - p10 * p10;
+    const double inv = 1.0 / det;
     it.pinv[0] = p11 * inv;   // (P^-1)_00
     it.pinv[1] = -p10 * inv;  // (P^-1)_10
     it.pinv[2] = p00 * inv;   // (P^-1)_11
+    // D of the next step = Nn_k / det(P)^(-1/2)
+    if (!it.half) xnext = a * sqrt(det);
+    it.dcarry[0] = xnext.x0;
+    it.dcarry[1] = xnext.x1;
+    it.dcarry[2] = xnext.x2;
   }
 }
 
@@ -217,6 +263,17 @@ static double unit_of(int prec) {
 
 using namespace gbs;
 
+namespace {
+struct StepTree {
+  int t;         // trajectory
+  int half;      // 1: tree over S of Sigma'|k; 0: tree over S u {k}
+  int n;         // modes of the tree (0 = no tree: Tor = 1)
+  int prec;
+  long long root_off;
+  ProbOut res;
+};
+}  // namespace
+
 extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_samples, uint64_t seed, int N_post,
                                  int max_attempts, const int* forced_clicks, int prec, uint8_t* patterns,
                                  double* p0_out, gbs_sample_stats* stats) {
@@ -237,10 +294,11 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
   gbs_status e;
   if ((e = ensure_sigma_real(ctx, st))) return e;
   const size_t sig_bytes = (size_t)4 * M * M * sizeof(double);
-  DevBuf work;
   const int T = n_samples;
-  // per trajectory: Sigma', click list (64 ints), pivot inverse (4 doubles), L rows (2 x (2M + 64) doubles)
-  const size_t per_traj = sig_bytes + 64 * sizeof(int) + 4 * sizeof(double) + ((size_t)4 * M + 256) * sizeof(double);
+  // per trajectory: Sigma', click list (64 ints), pivot inverse + s0 (4 doubles), carried D (4 doubles),
+  // L rows (2 x (2M + 64) doubles)
+  const size_t per_traj = sig_bytes + 64 * sizeof(int) + 8 * sizeof(double) + ((size_t)4 * M + 256) * sizeof(double);
+  DevBuf work;
   if ((e = dev_alloc(ctx, work, per_traj * T + sizeof(DecideOut) * (size_t)T + 4096))) return e;
   auto fail = [&](gbs_status code) {
     dev_free(ctx, work);
@@ -248,21 +306,22 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
   };
   unsigned char* base = (unsigned char*)work.ptr;
   std::vector<Traj> tr(T);
-  std::vector<double*> pinv(T), Lbuf(T);
+  std::vector<double*> pinv(T), dcarry(T), Lbuf(T);
   for (int t = 0; t < T; ++t) {
     unsigned char* p = base + per_traj * t;
     tr[t].sig = (double*)p;
     tr[t].clicks = (int*)(p + sig_bytes);
-    pinv[t] = (double*)(p + sig_bytes + 64 * sizeof(int));
-    Lbuf[t] = pinv[t] + 4;
+    pinv[t] = (double*)(p + sig_bytes + 64 * sizeof(int));  // [0..2] P^-1, [3] s0
+    dcarry[t] = pinv[t] + 4;
+    Lbuf[t] = pinv[t] + 8;
     tr[t].sample = t;
     tr[t].attempt = 0;
   }
   DecideOut* dout = (DecideOut*)(base + per_traj * T);
   std::vector<std::vector<int>> S(T);
-  std::vector<int> status(T, 0);  // 0 running, 1 done, 2 rejected for good
-  std::vector<double> kappa_prev(T, 1.0);
-  std::vector<int> prec_prev(T, GBS_PREC_FP64);
+  std::vector<int> status(T, 0);  // 0 running, 1 done, 2 rejected
+  std::vector<double> kappa_prev(T), relD(T);
+  std::vector<int> need_full(T, 1), prec_prev(T);
   std::vector<std::vector<char>> forced(T);
   if (forced_clicks) {
     for (int t = 0; t < T; ++t) {
@@ -270,12 +329,21 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
       for (int c = 0; c < N_post; ++c) forced[t][forced_clicks[(long long)t * N_post + c]] = 1;
     }
   }
+  // Bound on |delta p0|: half the near-tie threshold, so that a decision can
+  // differ from an exact evaluation only for draws already counted as near ties.
+  const double TOL = 5e-10;
+  auto pick = [&](double kp, int n) {
+    if (prec != GBS_PREC_AUTO) return prec;
+    const int ladder[3] = {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD};
+    for (int l = 0; l < 3; ++l)
+      if (4.0 * std::max(n, 1) * unit_of(ladder[l]) * kp * 2.0 < 0.5 * TOL) return ladder[l];
+    return (int)GBS_PREC_TD;
+  };
   gbs_sample_stats stt{};
   memset(patterns, 0xFF, (size_t)T * M);
   std::vector<int> wave(T);
   for (int t = 0; t < T; ++t) wave[t] = t;
   while (!wave.empty()) {
-    // (re)start the trajectories of this wave from the state
     for (int t : wave) {
       if ((e = check_cuda(ctx, cudaMemcpyAsync(tr[t].sig, st->sig_real.ptr, sig_bytes, cudaMemcpyDeviceToDevice,
                                                ctx->stream),
@@ -284,6 +352,8 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
       S[t].clear();
       tr[t].m = 0;
       kappa_prev[t] = 1.0;
+      relD[t] = 0.0;
+      need_full[t] = 1;
       prec_prev[t] = GBS_PREC_FP64;
     }
     std::vector<char> live(T, 0);
@@ -294,77 +364,79 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
       for (int t : wave)
         if (live[t]) act.push_back(t);
       if (act.empty()) break;
-      if ((e = stage_begin(ctx, act.size() * (sizeof(GatherItem) + sizeof(DecideItem) + sizeof(CondItem) + 16384) +
+      if ((e = stage_begin(ctx, act.size() * (2 * sizeof(GatherItem) + sizeof(DecideItem) + sizeof(CondItem) +
+                                              4 * 16384) +
                                     (1 << 16))))
         return fail(e);
-      // ---- roots Sigma'[S u {k}]
-      std::vector<GatherItem> gi(act.size());
-      std::vector<BatchTree> trees(act.size());
-      long long ent = 0;
-      for (size_t i = 0; i < act.size(); ++i) {
-        const int t = act[i];
-        const int n = tr[t].m + 1;
-        gi[i] = GatherItem{tr[t].sig, tr[t].clicks, ent, tr[t].m, k, M, 0};
-        trees[i] = BatchTree{n, ent};
-        ent += (long long)n * (2 * n + 1);
-      }
-      if ((e = dev_reserve(ctx, ctx->hbuf, (size_t)ent * sizeof(double)))) return fail(e);
-      const void* dgi = nullptr;
-      if ((e = stage(ctx, gi.data(), gi.size() * sizeof(GatherItem), &dgi))) return fail(e);
-      gather_kernel<<<(unsigned)act.size(), 128, 0, ctx->stream>>>((const GatherItem*)dgi, (double*)ctx->hbuf.ptr);
-      count_launch(ctx);
-      // ---- trees, precision chosen per trajectory and verified
-      std::vector<ProbOut> res(act.size());
-      std::vector<int> used(act.size());
-      std::vector<int> want(act.size());
-      for (size_t i = 0; i < act.size(); ++i) {
-        const int t = act[i];
-        if (prec != GBS_PREC_AUTO) {
-          want[i] = prec;
-          continue;
-        }
-        // predicted kappa: the last one, times 8 per click since (margin)
-        const double kp = kappa_prev[t] * 8.0;
-        const double n = tr[t].m + 1;
-        const int ladder[3] = {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD};
-        want[i] = GBS_PREC_TD;
-        for (int l = 0; l < 3; ++l)
-          if (4.0 * n * unit_of(ladder[l]) * kp * 4.0 < 1e-11) {
-            want[i] = ladder[l];
-            break;
-          }
-        want[i] = std::max(want[i], prec_prev[t]);
-      }
+      std::vector<StepTree> trees(act.size());
       std::vector<size_t> todo(act.size());
-      for (size_t i = 0; i < act.size(); ++i) todo[i] = i;
-      for (int round = 0; round < 3 && !todo.empty(); ++round) {
-        std::vector<size_t> next;
+      for (size_t i = 0; i < act.size(); ++i) {
+        const int t = act[i];
+        StepTree& q = trees[i];
+        q.t = t;
+        q.half = need_full[t] ? 0 : 1;
+        q.n = q.half ? tr[t].m : tr[t].m + 1;
+        q.prec = pick(kappa_prev[t] * (q.half ? 1.5 : 8.0), q.n);
+        todo[i] = i;
+      }
+      // rounds: evaluate, check, escalate failing trajectories to a full tree at a wider precision
+      for (int round = 0; round < 4 && !todo.empty(); ++round) {
+        std::vector<GatherItem> gi;
+        long long ent = 0;
+        for (size_t i : todo) {
+          StepTree& q = trees[i];
+          q.root_off = ent;
+          gi.push_back(GatherItem{tr[q.t].sig, tr[q.t].clicks, pinv[q.t] + 3, ent, tr[q.t].m, k, M, q.half});
+          const int d = 2 * std::max(q.n, 1);
+          ent += (long long)d * (d + 1) / 2;
+        }
+        if ((e = dev_reserve(ctx, ctx->hbuf, (size_t)ent * sizeof(double)))) return fail(e);
+        const void* dgi = nullptr;
+        if ((e = stage(ctx, gi.data(), gi.size() * sizeof(GatherItem), &dgi))) return fail(e);
+        gather_kernel<<<(unsigned)gi.size(), 128, 0, ctx->stream>>>((const GatherItem*)dgi, (double*)ctx->hbuf.ptr);
+        count_launch(ctx);
         for (int pv : {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD}) {
           std::vector<size_t> grp;
           for (size_t i : todo)
-            if (want[i] == pv) grp.push_back(i);
+            if (trees[i].prec == pv && trees[i].n > 0) grp.push_back(i);
           if (grp.empty()) continue;
           std::vector<BatchTree> sub(grp.size());
           std::vector<double> zero(grp.size(), 0.0);
-          for (size_t j = 0; j < grp.size(); ++j) sub[j] = trees[grp[j]];
+          for (size_t j = 0; j < grp.size(); ++j) sub[j] = BatchTree{trees[grp[j]].n, trees[grp[j]].root_off};
           std::vector<ProbOut> r(grp.size());
+          const auto tb = std::chrono::steady_clock::now();
           if ((e = batch_eval(ctx, pv, true, (int)grp.size(), sub.data(), ctx->hbuf.ptr, zero.data(), r.data())))
             return fail(e);
+          stt.tree_seconds[pv - 1] += std::chrono::duration<double>(std::chrono::steady_clock::now() - tb).count();
+          stt.trees[pv - 1] += (long long)grp.size();
           stt.steps += (long long)grp.size();
-          for (size_t j = 0; j < grp.size(); ++j) {
-            const size_t i = grp[j];
-            res[i] = r[j];
-            used[i] = pv;
-            if (r[j].status) return fail(set_error(ctx, GBS_ENOTPD, "sampler: a pivot block is not positive definite"));
-            const double exc = fabs(r[j].exc[0]), inc = fabs(r[j].inc[0]);
+          for (size_t j = 0; j < grp.size(); ++j) trees[grp[j]].res = r[j];
+        }
+        std::vector<size_t> next;
+        for (size_t i : todo) {
+          StepTree& q = trees[i];
+          if (q.n == 0) {  // half step with no clicks yet: Tor = 1 exactly
+            memset(&q.res, 0, sizeof(ProbOut));
+            q.res.tor[0] = 1.0;
+            q.res.abs_sum = 1.0;
+          }
+          if (q.res.status) return fail(set_error(ctx, GBS_ENOTPD, "sampler: a pivot block is not positive definite"));
+          const double u = unit_of(q.prec), n = std::max(q.n, 1);
+          double dp;
+          if (q.half) {
+            const double tor = fabs(q.res.tor[0]);
+            dp = (q.n ? 4.0 * n * u * q.res.abs_sum / std::max(tor, 1e-300) : 0.0) + 2e-16 + relD[q.t];
+          } else {
+            const double exc = fabs(q.res.exc[0]), inc = fabs(q.res.inc[0]);
             const double p0 = exc > 0 ? inc / exc : INFINITY;
-            const double n = trees[i].n;
-            const double dp = 4.0 * n * unit_of(pv) * r[j].abs_sum * (1.0 + p0) / std::max(exc, 1e-300);
-            if (prec == GBS_PREC_AUTO && !(dp < 1e-11) && pv != GBS_PREC_TD) {
-              want[i] = pv == GBS_PREC_FP64 ? GBS_PREC_DD : GBS_PREC_TD;
-              next.push_back(i);
-              stt.escalations++;
-            }
+            dp = 4.0 * n * u * q.res.abs_sum * (1.0 + p0) / std::max(exc, 1e-300);
+          }
+          if (prec == GBS_PREC_AUTO && !(dp < TOL) && !(q.prec == GBS_PREC_TD && !q.half)) {
+            q.half = 0;
+            q.n = tr[q.t].m + 1;
+            q.prec = std::min<int>(GBS_PREC_TD, std::max(q.prec + 1, (int)GBS_PREC_DD));
+            next.push_back(i);
+            stt.escalations++;
           }
         }
         todo.swap(next);
@@ -372,25 +444,37 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
       // ---- decide on the device
       std::vector<DecideItem> di(act.size());
       for (size_t i = 0; i < act.size(); ++i) {
-        const int t = act[i];
+        const StepTree& q = trees[i];
+        const int t = q.t;
         DecideItem d{};
         for (int c = 0; c < 3; ++c) {
-          d.inc[c] = res[i].inc[c];
-          d.exc[c] = res[i].exc[c];
+          d.inc[c] = q.half ? q.res.tor[c] : q.res.inc[c];  // half: the whole Torontonian of the tree over S
+          d.exc[c] = q.res.exc[c];
         }
         d.sig = tr[t].sig;
         d.clicks = tr[t].clicks;
         d.pinv = pinv[t];
+        d.dcarry = dcarry[t];
+        d.s0 = pinv[t] + 3;
         d.m = tr[t].m;
         d.k = k;
         d.step = step;
         d.sample = tr[t].sample;
         d.attempt = tr[t].attempt;
         d.forced = forced_clicks ? (int)forced[t][k] : -1;
+        d.half = q.half;
         di[i] = d;
-        const double exc = fabs(res[i].exc[0]);
-        kappa_prev[t] = exc > 0 ? res[i].abs_sum / exc : 1e300;
-        prec_prev[t] = used[i];
+        const double u = unit_of(q.prec), n = std::max(q.n, 1);
+        if (q.half) {
+          const double tor = fabs(q.res.tor[0]);
+          kappa_prev[t] = q.res.abs_sum / std::max(tor, 1e-300);
+          relD[t] = 4.0 * n * u * kappa_prev[t] + 2e-16;  // the carried D is (-1)^m Tor_k
+        } else {
+          const double exc = fabs(q.res.exc[0]), inc = fabs(q.res.inc[0]);
+          kappa_prev[t] = q.res.abs_sum / std::max(std::min(exc, inc), 1e-300);
+          relD[t] = 4.0 * n * u * q.res.abs_sum / std::max(inc, 1e-300) + 4e-16;
+        }
+        prec_prev[t] = q.prec;
       }
       const void* ddi = nullptr;
       if ((e = stage(ctx, di.data(), di.size() * sizeof(DecideItem), &ddi))) return fail(e);
@@ -410,6 +494,7 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
         const int t = act[i];
         if (p0_out) p0_out[(long long)tr[t].sample * M + step] = dec[i].p0;
         stt.near_ties += dec[i].near_tie;
+        need_full[t] = dec[i].click;
         if (dec[i].click) {
           S[t].push_back(k);
           tr[t].m++;
@@ -446,7 +531,6 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
         if ((e = check_cuda(ctx, cudaGetLastError(), "conditioning"))) return fail(e);
       }
     }
-    // finished trajectories -> patterns; rejected ones retry with the next attempt
     std::vector<int> next;
     for (int t : wave) {
       if (status[t] == 1) {
@@ -467,6 +551,7 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
   if ((e = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync"))) return fail(e);
   dev_free(ctx, work);
   stt.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  stt.cond_seconds = stt.seconds - stt.tree_seconds[0] - stt.tree_seconds[1] - stt.tree_seconds[2];
   if (stats) *stats = stt;
   for (int t = 0; t < T; ++t)
     if (status[t] != 1) return set_error(ctx, GBS_EREJECT, "postselection attempts exhausted for some samples");

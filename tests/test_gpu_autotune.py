@@ -25,7 +25,7 @@ def test_launch_shapes_agree(ctx):
     H = real_basis_block(oracle.sigma_inv_block(Sig, gi.random_modes(150, 17, seed=9)))
     ref, ref_abs = oracle.torontonian(H.astype(np.complex128))
     seen = []
-    for sub_e in (0, 3, 5, 7):
+    for sub_e in (0, 5, 6, 7):
         for d_top in (0, 4, 10):
             for grid in (0, 2):
                 ctx.set_tuning("dd", "real", sub_e, d_top, grid, 1 << 17)
