@@ -217,6 +217,66 @@ gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* st, int n_samples, uint64_t
                       const int* forced_clicks, int prec, uint8_t* patterns, double* p0_out,
                       gbs_sample_stats* stats);
 
+/* ---------------------------------------------------------- request loop -- */
+
+typedef enum { GBS_REQ_PROB = 0, GBS_REQ_SAMPLE = 1 } gbs_req_kind;
+
+typedef struct {
+  int kind;                /* gbs_req_kind */
+  const gbs_state* state;  /* must stay alive until the request is polled */
+  int N;                   /* PROB: click count; SAMPLE: N_post (0 = no postselection) */
+  const int* modes;        /* PROB: the N click modes (copied by gbs_submit) */
+  uint64_t seed;           /* SAMPLE: coin stream seed (as gbs_sample) */
+  int sample_index;        /* SAMPLE: sample index of the coin counter, 0 <= index < 2^20 */
+  int max_attempts;        /* SAMPLE: postselection attempts (>= 1) */
+  int prec;                /* gbs_prec (SAMPLE: AUTO, FP64, DD or TD) */
+  int basis;               /* PROB: gbs_basis */
+  double rel_tol;          /* PROB: as gbs_torontonian */
+} gbs_request;
+
+typedef struct {
+  int status;              /* GBS_OK, GBS_EREJECT (attempts exhausted), GBS_EPRECISION, GBS_ENOTPD, ... */
+  int kind;
+  gbs_prob prob;           /* PROB */
+  int n_clicks;            /* SAMPLE: clicked modes (at most 31) */
+  int clicks[64];
+  int attempts;            /* SAMPLE: attempts used */
+  double latency_s;        /* submit -> completion */
+  double queue_s;          /* submit -> admission */
+} gbs_result;
+
+typedef struct {
+  long long submitted, completed, refused, active, queued;
+  double p50_s, p99_s, mean_s;  /* latency percentiles of completed requests */
+  double busy_s, wall_s;        /* time the loop spent working / since start */
+  size_t arena_bytes, arena_in_use;
+  int last_error;
+} gbs_server_stats;
+
+/* Start the context's request loop: a worker thread that admits submitted
+ * requests in arrival order while their device footprint fits an arena of
+ * arena_bytes (allocated now; a sampling request needs 32 M^2 bytes plus about
+ * 32 M, a probability request only the shared tree workspace) and at most
+ * max_active sampling requests run at once.  Each loop iteration evaluates all
+ * newly admitted probability requests as one batch and advances every active
+ * sampling request by one measured mode, all their subset trees batched
+ * together, so late arrivals join running work at the next step.  A result is
+ * bitwise the same alone and in any mix.  While the loop runs, direct calls on
+ * the same context still work (they interleave with loop iterations).
+ * The paper has no counterpart (its runs were single jobs, Sec. III-IV). */
+gbs_status gbs_server_start(gbs_ctx* ctx, size_t arena_bytes, int max_active);
+/* Stop the loop (waits for the current iteration); unpolled results are dropped. */
+gbs_status gbs_server_stop(gbs_ctx* ctx);
+/* Queue a request; *ticket identifies it.  Errors: GBS_EINVAL (loop not running,
+ * bad descriptor), GBS_ENOMEM (footprint larger than the whole arena). */
+gbs_status gbs_submit(gbs_ctx* ctx, const gbs_request* req, uint64_t* ticket);
+/* Wait up to timeout_us microseconds (0: do not wait, < 0: until done) for a
+ * ticket.  GBS_OK: *out holds the result (its own status in out->status) and
+ * the ticket is consumed; GBS_PENDING: not finished; GBS_ENOTFOUND: unknown or
+ * already consumed ticket. */
+gbs_status gbs_poll(gbs_ctx* ctx, uint64_t ticket, gbs_result* out, int64_t timeout_us);
+gbs_status gbs_server_stats_get(gbs_ctx* ctx, gbs_server_stats* out);
+
 /* Launch shape of the batched enumeration, per (precision, basis):
  *   sub_e          0, or 5..7: levels each subtree CTA (2^sub_e threads, at
  *                  least one warp) expands in shared memory before its threads

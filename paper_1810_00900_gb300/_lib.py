@@ -47,6 +47,27 @@ class gbs_sample_stats(ctypes.Structure):
                 ("cond_seconds", ctypes.c_double)]
 
 
+class gbs_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("state", ctypes.c_void_p), ("N", ctypes.c_int),
+                ("modes", ctypes.POINTER(ctypes.c_int)), ("seed", ctypes.c_uint64), ("sample_index", ctypes.c_int),
+                ("max_attempts", ctypes.c_int), ("prec", ctypes.c_int), ("basis", ctypes.c_int),
+                ("rel_tol", ctypes.c_double)]
+
+
+class gbs_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("kind", ctypes.c_int), ("prob", gbs_prob), ("n_clicks", ctypes.c_int),
+                ("clicks", ctypes.c_int * 64), ("attempts", ctypes.c_int), ("latency_s", ctypes.c_double),
+                ("queue_s", ctypes.c_double)]
+
+
+class gbs_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("refused", ctypes.c_longlong),
+                ("active", ctypes.c_longlong), ("queued", ctypes.c_longlong), ("p50_s", ctypes.c_double),
+                ("p99_s", ctypes.c_double), ("mean_s", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("wall_s", ctypes.c_double), ("arena_bytes", ctypes.c_size_t), ("arena_in_use", ctypes.c_size_t),
+                ("last_error", ctypes.c_int)]
+
+
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -96,6 +117,11 @@ def load() -> ctypes.CDLL:
         "gbs_sample": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _ip,
                                       ctypes.c_int, ctypes.POINTER(ctypes.c_uint8), _dp,
                                       ctypes.POINTER(gbs_sample_stats)]),
+        "gbs_server_start": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.c_int]),
+        "gbs_server_stop": (ctypes.c_int, [_vp]),
+        "gbs_submit": (ctypes.c_int, [_vp, ctypes.POINTER(gbs_request), ctypes.POINTER(ctypes.c_uint64)]),
+        "gbs_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(gbs_result), ctypes.c_int64]),
+        "gbs_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(gbs_server_stats)]),
         "gbs_subset_sum": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]),
         "gbs_subset_sum_static": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     }
@@ -324,6 +350,58 @@ def sample(ctx: Context, st: State, n_samples: int, seed: int, N_post: int = 0, 
     sd["trees"] = list(sd["trees"])
     sd["tree_seconds"] = list(sd["tree_seconds"])
     return pats, p0, sd, status
+
+
+class Server:
+    """The context's request loop (gbs_server_start / gbs_submit / gbs_poll)."""
+
+    def __init__(self, ctx: Context, arena_bytes: int = 4 << 30, max_active: int = 64):
+        self.ctx = ctx
+        ctx.check(ctx.L.gbs_server_start(ctx.h, int(arena_bytes), int(max_active)))
+        self._keep = {}
+
+    def submit_prob(self, st: State, modes, prec: str = "auto", basis: str = "auto", rel_tol: float = 0.0) -> int:
+        m = np.ascontiguousarray(modes, dtype=np.int32)
+        r = gbs_request(kind=0, state=st.h, N=int(m.size), modes=_i(m) if m.size else None, seed=0,
+                        sample_index=0, max_attempts=1, prec=PREC[prec], basis=BASIS[basis], rel_tol=rel_tol)
+        t = ctypes.c_uint64()
+        self.ctx.check(self.ctx.L.gbs_submit(self.ctx.h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def submit_sample(self, st: State, seed: int, sample_index: int = 0, N_post: int = 0, max_attempts: int = 1,
+                      prec: str = "auto") -> int:
+        r = gbs_request(kind=1, state=st.h, N=int(N_post), modes=None, seed=seed & ((1 << 64) - 1),
+                        sample_index=int(sample_index), max_attempts=int(max_attempts), prec=PREC[prec], basis=1,
+                        rel_tol=0.0)
+        t = ctypes.c_uint64()
+        self.ctx.check(self.ctx.L.gbs_submit(self.ctx.h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, timeout_s: float = -1.0):
+        """None while pending; else a dict with the result."""
+        out = gbs_result()
+        us = -1 if timeout_s < 0 else int(timeout_s * 1e6)
+        st = self.ctx.L.gbs_poll(self.ctx.h, ctypes.c_uint64(ticket), ctypes.byref(out), ctypes.c_int64(us))
+        if st == PENDING:
+            return None
+        if st != OK:
+            raise GbsError(st, "gbs_poll")
+        res = {"status": out.status, "kind": out.kind, "latency_s": out.latency_s, "queue_s": out.queue_s,
+               "attempts": out.attempts}
+        if out.kind == 0:
+            res["prob"] = _prob(out.prob)
+        else:
+            res["clicks"] = sorted(out.clicks[i] for i in range(out.n_clicks))
+        return res
+
+    def stats(self) -> dict:
+        s = gbs_server_stats()
+        self.ctx.check(self.ctx.L.gbs_server_stats_get(self.ctx.h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in gbs_server_stats._fields_}
+
+    def stop(self):
+        if self.ctx.h:
+            self.ctx.L.gbs_server_stop(self.ctx.h)
 
 
 def subset_sum(ctx: Context, G, basis: str = "complex", prec: str = "fp64"):

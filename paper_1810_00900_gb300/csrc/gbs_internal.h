@@ -135,6 +135,35 @@ gbs_status batch_eval(gbs_ctx* ctx, int prec, bool real, int ntrees, const Batch
 // The tuning in force for (prec, basis) -- the autotuner's choice when one was made.
 const BatchTune& batch_tune_for(gbs_ctx* ctx, int prec, bool real);
 
+// One chain-rule trajectory (gbs_sampler.cu): host bookkeeping plus device
+// buffers inside a block of traj_bytes(M) bytes bound by traj_bind().
+struct Trajectory {
+  enum { kRunning = 0, kDone = 1, kRejected = 2 };
+  gbs_state* st = nullptr;
+  int M = 0;
+  unsigned long long seed = 0;
+  int sample = 0, attempt = 0, N_post = 0;
+  std::vector<char> forced;  // empty: free draws; else 1 where the outcome is a click
+  bool want_p0 = false;
+  // device
+  double* sig = nullptr;  // conditioned Sigma' (2M x 2M, real x/p basis)
+  int* clicks = nullptr;
+  double* pinv = nullptr;
+  double* dcarry = nullptr;
+  double* L = nullptr;
+  // host
+  int step = 0, m = 0, need_full = 1, state = kRunning;
+  std::vector<int> S;
+  double kappa_prev = 1.0, relD = 0.0;
+  std::vector<double> p0;
+};
+size_t traj_bytes(int M);
+void traj_bind(Trajectory& tj, gbs_state* st, unsigned char* mem);
+gbs_status traj_start(gbs_ctx* ctx, Trajectory& tj);
+gbs_status ensure_sigma_real(gbs_ctx* ctx, gbs_state* st);
+gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, int prec, gbs_sample_stats& stt);
+double unit_of(int prec);
+
 // Up to 32 click modes passed by value as a kernel argument.
 struct ModeList {
   int m[32];

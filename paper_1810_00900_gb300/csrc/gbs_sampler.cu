@@ -64,16 +64,6 @@ __global__ void sigma_real_kernel(const cplx<double>* __restrict__ V, int M, dou
   S[r0 * D + c0 + 1] = -0.5 * (h00.im - h01.im + h10.im - h11.im);
 }
 
-struct Traj {
-  double* sig;       // this trajectory's Sigma' (2M x 2M, full, row-major)
-  int* clicks;       // device list of clicked modes (capacity kMaxClicks + 1)
-  int m;             // clicks so far
-  int sample;        // sample index (RNG stream)
-  int attempt;
-  int tree;          // index of its tree in this step's batch (-1: idle)
-  long long root_off;
-};
-
 struct GatherItem {
   const double* sig;
   const int* clicks;
@@ -126,7 +116,8 @@ struct DecideItem {
   double* pinv;           // out: scaled inverse of the 2x2 pivot block (3 values)
   double* dcarry;         // in (half) / out: D of the next step, triple-double
   const double* s0;       // half: det(Sigma'_k)^(-1/2)
-  int m, k, step, sample, attempt, forced, half, pad1;
+  unsigned long long seed;
+  int m, k, step, sample, attempt, forced, half, M;
 };
 
 struct DecideOut {
@@ -142,11 +133,12 @@ __device__ __forceinline__ double splitmix_u(unsigned long long seed, unsigned l
   return (double)(z >> 11) * 0x1p-53;
 }
 
-__global__ void decide_kernel(const DecideItem* __restrict__ items, int nitems, unsigned long long seed, int M,
-                              DecideOut* __restrict__ out) {
+__global__ void decide_kernel(const DecideItem* __restrict__ items, int nitems, DecideOut* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nitems) return;
   const DecideItem it = items[i];
+  const int M = it.M;
+  const unsigned long long seed = it.seed;
   const double sgn = (it.m & 1) ? -1.0 : 1.0;  // (-1)^m
   // Nn (a) and D (b) in triple-double, then p0 = a/b by two correction steps
   td a, b, xnext;
@@ -204,7 +196,7 @@ struct CondItem {
   const double* pinv;
   double* L;       // 2 x A scratch: L row i at L[2i], L[2i+1]
   long long entry_begin;
-  int m, k, A, pad;  // A = 2k + 2m active rows
+  int m, k, A, M;  // A = 2k + 2m active rows
 };
 
 __device__ __forceinline__ long long active_row(int i, int k, const int* clicks) {
@@ -212,11 +204,11 @@ __device__ __forceinline__ long long active_row(int i, int k, const int* clicks)
 }
 
 // L_i = Sigma'[i, k-block] P^-1 for every active row i.
-__global__ void cond_L_kernel(const CondItem* __restrict__ items, int M) {
+__global__ void cond_L_kernel(const CondItem* __restrict__ items) {
   const CondItem it = items[blockIdx.y];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= it.A) return;
-  const long long D = 2LL * M;
+  const long long D = 2LL * it.M;
   const long long ri = active_row(i, it.k, it.clicks);
   const double u0 = it.sig[ri * D + 2LL * it.k], u1 = it.sig[ri * D + 2LL * it.k + 1];
   it.L[2 * i] = fma(u0, it.pinv[0], u1 * it.pinv[1]);
@@ -224,7 +216,7 @@ __global__ void cond_L_kernel(const CondItem* __restrict__ items, int M) {
 }
 
 // Sigma'[i, j] -= L_i . Sigma'[k-block, j] over the active block.
-__global__ void cond_update_kernel(const CondItem* __restrict__ items, int nitems, long long total, int M) {
+__global__ void cond_update_kernel(const CondItem* __restrict__ items, int nitems, long long total) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
   int lo = 0, hi = nitems - 1;
@@ -235,7 +227,7 @@ __global__ void cond_update_kernel(const CondItem* __restrict__ items, int nitem
   const CondItem it = items[lo];
   const long long e = t - it.entry_begin;
   const int i = (int)(e / it.A), j = (int)(e % it.A);
-  const long long D = 2LL * M;
+  const long long D = 2LL * it.M;
   const long long ri = active_row(i, it.k, it.clicks), rj = active_row(j, it.k, it.clicks);
   const double w0 = it.sig[(2LL * it.k) * D + rj], w1 = it.sig[(2LL * it.k + 1) * D + rj];
   double* x = it.sig + ri * D + rj;
@@ -244,7 +236,7 @@ __global__ void cond_update_kernel(const CondItem* __restrict__ items, int nitem
 
 }  // namespace
 
-static gbs_status ensure_sigma_real(gbs_ctx* ctx, gbs_state* st) {
+gbs_status ensure_sigma_real(gbs_ctx* ctx, gbs_state* st) {
   if (st->sig_real.ptr) return GBS_OK;
   const long long M = st->M;
   gbs_status e;
@@ -255,17 +247,48 @@ static gbs_status ensure_sigma_real(gbs_ctx* ctx, gbs_state* st) {
   return check_cuda(ctx, cudaGetLastError(), "sigma real");
 }
 
-static double unit_of(int prec) {
+double unit_of(int prec) {
   return prec == GBS_PREC_FP64 ? 0x1p-53 : prec == GBS_PREC_DD ? 0x1p-102 : 0x1p-152;
 }
 
-}  // namespace gbs
 
-using namespace gbs;
+size_t traj_bytes(int M) {
+  return (size_t)4 * M * M * sizeof(double) + 64 * sizeof(int) + 8 * sizeof(double) +
+         ((size_t)4 * M + 256) * sizeof(double);
+}
+
+void traj_bind(Trajectory& tj, gbs_state* st, unsigned char* mem) {
+  tj.st = st;
+  tj.M = st->M;
+  const size_t sig_bytes = (size_t)4 * tj.M * tj.M * sizeof(double);
+  tj.sig = (double*)mem;
+  tj.clicks = (int*)(mem + sig_bytes);
+  tj.pinv = (double*)(mem + sig_bytes + 64 * sizeof(int));  // [0..2] P^-1, [3] s0
+  tj.dcarry = tj.pinv + 4;
+  tj.L = tj.pinv + 8;
+}
+
+gbs_status traj_start(gbs_ctx* ctx, Trajectory& tj) {
+  gbs_status e;
+  if ((e = ensure_sigma_real(ctx, tj.st))) return e;
+  if ((e = check_cuda(ctx, cudaMemcpyAsync(tj.sig, tj.st->sig_real.ptr, (size_t)4 * tj.M * tj.M * sizeof(double),
+                                           cudaMemcpyDeviceToDevice, ctx->stream),
+                      "init trajectory")))
+    return e;
+  tj.step = 0;
+  tj.m = 0;
+  tj.S.clear();
+  tj.kappa_prev = 1.0;
+  tj.relD = 0.0;
+  tj.need_full = 1;
+  tj.state = Trajectory::kRunning;
+  if (tj.want_p0) tj.p0.assign(tj.M, 0.0);
+  return GBS_OK;
+}
 
 namespace {
 struct StepTree {
-  int t;         // trajectory
+  Trajectory* tj;
   int half;      // 1: tree over S of Sigma'|k; 0: tree over S u {k}
   int n;         // modes of the tree (0 = no tree: Tor = 1)
   int prec;
@@ -273,6 +296,199 @@ struct StepTree {
   ProbOut res;
 };
 }  // namespace
+
+// Advance every running trajectory of `jobs` by one measured mode.  The jobs may
+// belong to different states, sizes and step positions; all their trees of a
+// given precision run as one batch.  A trajectory that finishes becomes kDone,
+// one abandoned by postselection kRejected (the caller restarts or drops it).
+gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, int prec, gbs_sample_stats& stt) {
+  std::vector<Trajectory*> act;
+  for (Trajectory* t : jobs)
+    if (t->state == Trajectory::kRunning) act.push_back(t);
+  if (act.empty()) return GBS_OK;
+  gbs_status e;
+  // Bound on |delta p0|: half the near-tie threshold, so that a decision can
+  // differ from an exact evaluation only for draws already counted as near ties.
+  const double TOL = 5e-10;
+  auto pick = [&](double kp, int n) {
+    if (prec != GBS_PREC_AUTO) return prec;
+    const int ladder[3] = {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD};
+    for (int l = 0; l < 3; ++l)
+      if (4.0 * std::max(n, 1) * unit_of(ladder[l]) * kp * 2.0 < 0.5 * TOL) return ladder[l];
+    return (int)GBS_PREC_TD;
+  };
+  if ((e = stage_begin(ctx, act.size() * (2 * sizeof(GatherItem) + sizeof(DecideItem) + sizeof(CondItem) + 4 * 16384) +
+                                (1 << 16))))
+    return e;
+  std::vector<StepTree> trees(act.size());
+  std::vector<size_t> todo(act.size());
+  for (size_t i = 0; i < act.size(); ++i) {
+    Trajectory* t = act[i];
+    StepTree& q = trees[i];
+    q.tj = t;
+    q.half = t->need_full ? 0 : 1;
+    q.n = q.half ? t->m : t->m + 1;
+    q.prec = pick(t->kappa_prev * (q.half ? 1.5 : 8.0), q.n);
+    todo[i] = i;
+  }
+  for (int round = 0; round < 4 && !todo.empty(); ++round) {
+    std::vector<GatherItem> gi;
+    long long ent = 0;
+    for (size_t i : todo) {
+      StepTree& q = trees[i];
+      Trajectory* t = q.tj;
+      q.root_off = ent;
+      gi.push_back(GatherItem{t->sig, t->clicks, t->pinv + 3, ent, t->m, t->M - 1 - t->step, t->M, q.half});
+      const int d = 2 * std::max(q.n, 1);
+      ent += (long long)d * (d + 1) / 2;
+    }
+    if ((e = dev_reserve(ctx, ctx->hbuf, (size_t)ent * sizeof(double)))) return e;
+    const void* dgi = nullptr;
+    if ((e = stage(ctx, gi.data(), gi.size() * sizeof(GatherItem), &dgi))) return e;
+    gather_kernel<<<(unsigned)gi.size(), 128, 0, ctx->stream>>>((const GatherItem*)dgi, (double*)ctx->hbuf.ptr);
+    count_launch(ctx);
+    for (int pv : {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD}) {
+      std::vector<size_t> grp;
+      for (size_t i : todo)
+        if (trees[i].prec == pv && trees[i].n > 0) grp.push_back(i);
+      if (grp.empty()) continue;
+      std::vector<BatchTree> sub(grp.size());
+      std::vector<double> zero(grp.size(), 0.0);
+      for (size_t j = 0; j < grp.size(); ++j) sub[j] = BatchTree{trees[grp[j]].n, trees[grp[j]].root_off};
+      std::vector<ProbOut> r(grp.size());
+      const auto tb = std::chrono::steady_clock::now();
+      if ((e = batch_eval(ctx, pv, true, (int)grp.size(), sub.data(), ctx->hbuf.ptr, zero.data(), r.data())))
+        return e;
+      stt.tree_seconds[pv - 1] += std::chrono::duration<double>(std::chrono::steady_clock::now() - tb).count();
+      stt.trees[pv - 1] += (long long)grp.size();
+      stt.steps += (long long)grp.size();
+      for (size_t j = 0; j < grp.size(); ++j) trees[grp[j]].res = r[j];
+    }
+    std::vector<size_t> next;
+    for (size_t i : todo) {
+      StepTree& q = trees[i];
+      if (q.n == 0) {  // half step with no clicks yet: Tor = 1 exactly
+        memset(&q.res, 0, sizeof(ProbOut));
+        q.res.tor[0] = 1.0;
+        q.res.abs_sum = 1.0;
+      }
+      if (q.res.status) return set_error(ctx, GBS_ENOTPD, "sampler: a pivot block is not positive definite");
+      const double u = unit_of(q.prec), n = std::max(q.n, 1);
+      double dp;
+      if (q.half) {
+        const double tor = fabs(q.res.tor[0]);
+        dp = (q.n ? 4.0 * n * u * q.res.abs_sum / std::max(tor, 1e-300) : 0.0) + 2e-16 + q.tj->relD;
+      } else {
+        const double exc = fabs(q.res.exc[0]), inc = fabs(q.res.inc[0]);
+        const double p0 = exc > 0 ? inc / exc : INFINITY;
+        dp = 4.0 * n * u * q.res.abs_sum * (1.0 + p0) / std::max(exc, 1e-300);
+      }
+      if (prec == GBS_PREC_AUTO && !(dp < TOL) && !(q.prec == GBS_PREC_TD && !q.half)) {
+        q.half = 0;
+        q.n = q.tj->m + 1;
+        q.prec = std::min<int>(GBS_PREC_TD, std::max(q.prec + 1, (int)GBS_PREC_DD));
+        next.push_back(i);
+        stt.escalations++;
+      }
+    }
+    todo.swap(next);
+  }
+  // ---- decide on the device
+  std::vector<DecideItem> di(act.size());
+  for (size_t i = 0; i < act.size(); ++i) {
+    const StepTree& q = trees[i];
+    Trajectory* t = q.tj;
+    DecideItem d{};
+    for (int c = 0; c < 3; ++c) {
+      d.inc[c] = q.half ? q.res.tor[c] : q.res.inc[c];  // half: the whole Torontonian of the tree over S
+      d.exc[c] = q.res.exc[c];
+    }
+    const int k = t->M - 1 - t->step;
+    d.sig = t->sig;
+    d.clicks = t->clicks;
+    d.pinv = t->pinv;
+    d.dcarry = t->dcarry;
+    d.s0 = t->pinv + 3;
+    d.seed = t->seed;
+    d.m = t->m;
+    d.k = k;
+    d.step = t->step;
+    d.sample = t->sample;
+    d.attempt = t->attempt;
+    d.forced = t->forced.empty() ? -1 : (int)t->forced[k];
+    d.half = q.half;
+    d.M = t->M;
+    di[i] = d;
+    const double u = unit_of(q.prec), n = std::max(q.n, 1);
+    if (q.half) {
+      const double tor = fabs(q.res.tor[0]);
+      t->kappa_prev = q.res.abs_sum / std::max(tor, 1e-300);
+      t->relD = 4.0 * n * u * t->kappa_prev + 2e-16;  // the carried D is (-1)^m Tor_k
+    } else {
+      const double exc = fabs(q.res.exc[0]), inc = fabs(q.res.inc[0]);
+      t->kappa_prev = q.res.abs_sum / std::max(std::min(exc, inc), 1e-300);
+      t->relD = 4.0 * n * u * q.res.abs_sum / std::max(inc, 1e-300) + 4e-16;
+    }
+  }
+  const void* ddi = nullptr;
+  if ((e = stage(ctx, di.data(), di.size() * sizeof(DecideItem), &ddi))) return e;
+  if ((e = dev_reserve(ctx, ctx->out, act.size() * sizeof(DecideOut) + 64))) return e;
+  DecideOut* dout = (DecideOut*)ctx->out.ptr;
+  decide_kernel<<<(unsigned)((act.size() + 63) / 64), 64, 0, ctx->stream>>>((const DecideItem*)ddi, (int)act.size(),
+                                                                            dout);
+  count_launch(ctx);
+  std::vector<DecideOut> dec(act.size());
+  if ((e = check_cuda(ctx, cudaMemcpyAsync(dec.data(), dout, act.size() * sizeof(DecideOut), cudaMemcpyDeviceToHost,
+                                           ctx->stream),
+                      "decide readback")) ||
+      (e = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync")))
+    return e;
+  // ---- bookkeeping, postselection, conditioning of the dark modes
+  std::vector<CondItem> ci;
+  long long entries = 0;
+  for (size_t i = 0; i < act.size(); ++i) {
+    Trajectory* t = act[i];
+    const int k = t->M - 1 - t->step;
+    if (t->want_p0) t->p0[t->step] = dec[i].p0;
+    stt.near_ties += dec[i].near_tie;
+    t->need_full = dec[i].click;
+    if (dec[i].click) {
+      t->S.push_back(k);
+      t->m++;
+    }
+    const bool free_run = t->forced.empty();
+    if ((t->N_post > 0 && free_run && (t->m > t->N_post || t->m + k < t->N_post)) ||
+        (free_run && t->m > kMaxClicks)) {
+      t->state = Trajectory::kRejected;
+      stt.rejections++;
+      continue;
+    }
+    if (!dec[i].click && k > 0) {
+      const int A = 2 * k + 2 * t->m;
+      ci.push_back(CondItem{t->sig, t->clicks, t->pinv, t->L, entries, t->m, k, A, t->M});
+      entries += (long long)A * A;
+    }
+    t->step++;
+    if (k == 0) t->state = Trajectory::kDone;
+  }
+  if (!ci.empty()) {
+    const void* dci = nullptr;
+    if ((e = stage(ctx, ci.data(), ci.size() * sizeof(CondItem), &dci))) return e;
+    int amax = 0;
+    for (const CondItem& c : ci) amax = std::max(amax, c.A);
+    dim3 gl((amax + 255) / 256, (unsigned)ci.size());
+    cond_L_kernel<<<gl, 256, 0, ctx->stream>>>((const CondItem*)dci);
+    cond_update_kernel<<<(unsigned)((entries + 255) / 256), 256, 0, ctx->stream>>>((const CondItem*)dci,
+                                                                                   (int)ci.size(), entries);
+    count_launch(ctx, 2);
+    if ((e = check_cuda(ctx, cudaGetLastError(), "conditioning"))) return e;
+  }
+  return GBS_OK;
+}
+
+}  // namespace gbs
+
+using namespace gbs;
 
 extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_samples, uint64_t seed, int N_post,
                                  int max_attempts, const int* forced_clicks, int prec, uint8_t* patterns,
@@ -291,269 +507,61 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
       if (forced_clicks[i] < 0 || forced_clicks[i] >= M) return set_error(ctx, GBS_EINVAL, "forced click out of range");
   }
   const auto t_start = std::chrono::steady_clock::now();
-  gbs_status e;
-  if ((e = ensure_sigma_real(ctx, st))) return e;
-  const size_t sig_bytes = (size_t)4 * M * M * sizeof(double);
   const int T = n_samples;
-  // per trajectory: Sigma', click list (64 ints), pivot inverse + s0 (4 doubles), carried D (4 doubles),
-  // L rows (2 x (2M + 64) doubles)
-  const size_t per_traj = sig_bytes + 64 * sizeof(int) + 8 * sizeof(double) + ((size_t)4 * M + 256) * sizeof(double);
+  const size_t per = traj_bytes(M);
   DevBuf work;
-  if ((e = dev_alloc(ctx, work, per_traj * T + sizeof(DecideOut) * (size_t)T + 4096))) return e;
+  gbs_status e;
+  if ((e = dev_alloc(ctx, work, per * T))) return e;
   auto fail = [&](gbs_status code) {
     dev_free(ctx, work);
     return code;
   };
-  unsigned char* base = (unsigned char*)work.ptr;
-  std::vector<Traj> tr(T);
-  std::vector<double*> pinv(T), dcarry(T), Lbuf(T);
+  std::vector<Trajectory> tr(T);
+  std::vector<Trajectory*> ptrs(T);
   for (int t = 0; t < T; ++t) {
-    unsigned char* p = base + per_traj * t;
-    tr[t].sig = (double*)p;
-    tr[t].clicks = (int*)(p + sig_bytes);
-    pinv[t] = (double*)(p + sig_bytes + 64 * sizeof(int));  // [0..2] P^-1, [3] s0
-    dcarry[t] = pinv[t] + 4;
-    Lbuf[t] = pinv[t] + 8;
+    traj_bind(tr[t], st, (unsigned char*)work.ptr + per * t);
+    tr[t].seed = seed;
     tr[t].sample = t;
     tr[t].attempt = 0;
-  }
-  DecideOut* dout = (DecideOut*)(base + per_traj * T);
-  std::vector<std::vector<int>> S(T);
-  std::vector<int> status(T, 0);  // 0 running, 1 done, 2 rejected
-  std::vector<double> kappa_prev(T), relD(T);
-  std::vector<int> need_full(T, 1), prec_prev(T);
-  std::vector<std::vector<char>> forced(T);
-  if (forced_clicks) {
-    for (int t = 0; t < T; ++t) {
-      forced[t].assign(M, 0);
-      for (int c = 0; c < N_post; ++c) forced[t][forced_clicks[(long long)t * N_post + c]] = 1;
+    tr[t].N_post = N_post;
+    tr[t].want_p0 = p0_out != nullptr;
+    if (forced_clicks) {
+      tr[t].forced.assign(M, 0);
+      for (int c = 0; c < N_post; ++c) tr[t].forced[forced_clicks[(long long)t * N_post + c]] = 1;
     }
+    if ((e = traj_start(ctx, tr[t]))) return fail(e);
+    ptrs[t] = &tr[t];
   }
-  // Bound on |delta p0|: half the near-tie threshold, so that a decision can
-  // differ from an exact evaluation only for draws already counted as near ties.
-  const double TOL = 5e-10;
-  auto pick = [&](double kp, int n) {
-    if (prec != GBS_PREC_AUTO) return prec;
-    const int ladder[3] = {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD};
-    for (int l = 0; l < 3; ++l)
-      if (4.0 * std::max(n, 1) * unit_of(ladder[l]) * kp * 2.0 < 0.5 * TOL) return ladder[l];
-    return (int)GBS_PREC_TD;
-  };
   gbs_sample_stats stt{};
   memset(patterns, 0xFF, (size_t)T * M);
-  std::vector<int> wave(T);
-  for (int t = 0; t < T; ++t) wave[t] = t;
-  while (!wave.empty()) {
-    for (int t : wave) {
-      if ((e = check_cuda(ctx, cudaMemcpyAsync(tr[t].sig, st->sig_real.ptr, sig_bytes, cudaMemcpyDeviceToDevice,
-                                               ctx->stream),
-                          "init trajectory")))
-        return fail(e);
-      S[t].clear();
-      tr[t].m = 0;
-      kappa_prev[t] = 1.0;
-      relD[t] = 0.0;
-      need_full[t] = 1;
-      prec_prev[t] = GBS_PREC_FP64;
+  for (;;) {
+    bool any = false;
+    for (Trajectory& t : tr) {
+      if (t.state == Trajectory::kRejected && t.attempt + 1 < max_attempts) {
+        t.attempt++;
+        if ((e = traj_start(ctx, t))) return fail(e);
+      }
+      any |= t.state == Trajectory::kRunning;
     }
-    std::vector<char> live(T, 0);
-    for (int t : wave) live[t] = 1;
-    for (int step = 0; step < M; ++step) {
-      const int k = M - 1 - step;
-      std::vector<int> act;
-      for (int t : wave)
-        if (live[t]) act.push_back(t);
-      if (act.empty()) break;
-      if ((e = stage_begin(ctx, act.size() * (2 * sizeof(GatherItem) + sizeof(DecideItem) + sizeof(CondItem) +
-                                              4 * 16384) +
-                                    (1 << 16))))
-        return fail(e);
-      std::vector<StepTree> trees(act.size());
-      std::vector<size_t> todo(act.size());
-      for (size_t i = 0; i < act.size(); ++i) {
-        const int t = act[i];
-        StepTree& q = trees[i];
-        q.t = t;
-        q.half = need_full[t] ? 0 : 1;
-        q.n = q.half ? tr[t].m : tr[t].m + 1;
-        q.prec = pick(kappa_prev[t] * (q.half ? 1.5 : 8.0), q.n);
-        todo[i] = i;
-      }
-      // rounds: evaluate, check, escalate failing trajectories to a full tree at a wider precision
-      for (int round = 0; round < 4 && !todo.empty(); ++round) {
-        std::vector<GatherItem> gi;
-        long long ent = 0;
-        for (size_t i : todo) {
-          StepTree& q = trees[i];
-          q.root_off = ent;
-          gi.push_back(GatherItem{tr[q.t].sig, tr[q.t].clicks, pinv[q.t] + 3, ent, tr[q.t].m, k, M, q.half});
-          const int d = 2 * std::max(q.n, 1);
-          ent += (long long)d * (d + 1) / 2;
-        }
-        if ((e = dev_reserve(ctx, ctx->hbuf, (size_t)ent * sizeof(double)))) return fail(e);
-        const void* dgi = nullptr;
-        if ((e = stage(ctx, gi.data(), gi.size() * sizeof(GatherItem), &dgi))) return fail(e);
-        gather_kernel<<<(unsigned)gi.size(), 128, 0, ctx->stream>>>((const GatherItem*)dgi, (double*)ctx->hbuf.ptr);
-        count_launch(ctx);
-        for (int pv : {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD}) {
-          std::vector<size_t> grp;
-          for (size_t i : todo)
-            if (trees[i].prec == pv && trees[i].n > 0) grp.push_back(i);
-          if (grp.empty()) continue;
-          std::vector<BatchTree> sub(grp.size());
-          std::vector<double> zero(grp.size(), 0.0);
-          for (size_t j = 0; j < grp.size(); ++j) sub[j] = BatchTree{trees[grp[j]].n, trees[grp[j]].root_off};
-          std::vector<ProbOut> r(grp.size());
-          const auto tb = std::chrono::steady_clock::now();
-          if ((e = batch_eval(ctx, pv, true, (int)grp.size(), sub.data(), ctx->hbuf.ptr, zero.data(), r.data())))
-            return fail(e);
-          stt.tree_seconds[pv - 1] += std::chrono::duration<double>(std::chrono::steady_clock::now() - tb).count();
-          stt.trees[pv - 1] += (long long)grp.size();
-          stt.steps += (long long)grp.size();
-          for (size_t j = 0; j < grp.size(); ++j) trees[grp[j]].res = r[j];
-        }
-        std::vector<size_t> next;
-        for (size_t i : todo) {
-          StepTree& q = trees[i];
-          if (q.n == 0) {  // half step with no clicks yet: Tor = 1 exactly
-            memset(&q.res, 0, sizeof(ProbOut));
-            q.res.tor[0] = 1.0;
-            q.res.abs_sum = 1.0;
-          }
-          if (q.res.status) return fail(set_error(ctx, GBS_ENOTPD, "sampler: a pivot block is not positive definite"));
-          const double u = unit_of(q.prec), n = std::max(q.n, 1);
-          double dp;
-          if (q.half) {
-            const double tor = fabs(q.res.tor[0]);
-            dp = (q.n ? 4.0 * n * u * q.res.abs_sum / std::max(tor, 1e-300) : 0.0) + 2e-16 + relD[q.t];
-          } else {
-            const double exc = fabs(q.res.exc[0]), inc = fabs(q.res.inc[0]);
-            const double p0 = exc > 0 ? inc / exc : INFINITY;
-            dp = 4.0 * n * u * q.res.abs_sum * (1.0 + p0) / std::max(exc, 1e-300);
-          }
-          if (prec == GBS_PREC_AUTO && !(dp < TOL) && !(q.prec == GBS_PREC_TD && !q.half)) {
-            q.half = 0;
-            q.n = tr[q.t].m + 1;
-            q.prec = std::min<int>(GBS_PREC_TD, std::max(q.prec + 1, (int)GBS_PREC_DD));
-            next.push_back(i);
-            stt.escalations++;
-          }
-        }
-        todo.swap(next);
-      }
-      // ---- decide on the device
-      std::vector<DecideItem> di(act.size());
-      for (size_t i = 0; i < act.size(); ++i) {
-        const StepTree& q = trees[i];
-        const int t = q.t;
-        DecideItem d{};
-        for (int c = 0; c < 3; ++c) {
-          d.inc[c] = q.half ? q.res.tor[c] : q.res.inc[c];  // half: the whole Torontonian of the tree over S
-          d.exc[c] = q.res.exc[c];
-        }
-        d.sig = tr[t].sig;
-        d.clicks = tr[t].clicks;
-        d.pinv = pinv[t];
-        d.dcarry = dcarry[t];
-        d.s0 = pinv[t] + 3;
-        d.m = tr[t].m;
-        d.k = k;
-        d.step = step;
-        d.sample = tr[t].sample;
-        d.attempt = tr[t].attempt;
-        d.forced = forced_clicks ? (int)forced[t][k] : -1;
-        d.half = q.half;
-        di[i] = d;
-        const double u = unit_of(q.prec), n = std::max(q.n, 1);
-        if (q.half) {
-          const double tor = fabs(q.res.tor[0]);
-          kappa_prev[t] = q.res.abs_sum / std::max(tor, 1e-300);
-          relD[t] = 4.0 * n * u * kappa_prev[t] + 2e-16;  // the carried D is (-1)^m Tor_k
-        } else {
-          const double exc = fabs(q.res.exc[0]), inc = fabs(q.res.inc[0]);
-          kappa_prev[t] = q.res.abs_sum / std::max(std::min(exc, inc), 1e-300);
-          relD[t] = 4.0 * n * u * q.res.abs_sum / std::max(inc, 1e-300) + 4e-16;
-        }
-        prec_prev[t] = q.prec;
-      }
-      const void* ddi = nullptr;
-      if ((e = stage(ctx, di.data(), di.size() * sizeof(DecideItem), &ddi))) return fail(e);
-      decide_kernel<<<(unsigned)((act.size() + 63) / 64), 64, 0, ctx->stream>>>((const DecideItem*)ddi,
-                                                                                (int)act.size(), seed, M, dout);
-      count_launch(ctx);
-      std::vector<DecideOut> dec(act.size());
-      if ((e = check_cuda(ctx, cudaMemcpyAsync(dec.data(), dout, act.size() * sizeof(DecideOut),
-                                               cudaMemcpyDeviceToHost, ctx->stream),
-                          "decide readback")) ||
-          (e = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync")))
-        return fail(e);
-      // ---- bookkeeping, postselection, conditioning of the dark modes
-      std::vector<CondItem> ci;
-      long long entries = 0;
-      for (size_t i = 0; i < act.size(); ++i) {
-        const int t = act[i];
-        if (p0_out) p0_out[(long long)tr[t].sample * M + step] = dec[i].p0;
-        stt.near_ties += dec[i].near_tie;
-        need_full[t] = dec[i].click;
-        if (dec[i].click) {
-          S[t].push_back(k);
-          tr[t].m++;
-        }
-        const int mcount = tr[t].m;
-        bool reject = false;
-        if (N_post > 0 && !forced_clicks && (mcount > N_post || mcount + k < N_post)) reject = true;
-        if (!forced_clicks && mcount > kMaxClicks) reject = true;
-        if (reject) {
-          live[t] = 0;
-          status[t] = 2;
-          continue;
-        }
-        if (!dec[i].click && k > 0) {
-          const int A = 2 * k + 2 * mcount;
-          ci.push_back(CondItem{tr[t].sig, tr[t].clicks, pinv[t], Lbuf[t], entries, mcount, k, A, 0});
-          entries += (long long)A * A;
-        }
-        if (k == 0) {
-          live[t] = 0;
-          status[t] = 1;
-        }
-      }
-      if (!ci.empty()) {
-        const void* dci = nullptr;
-        if ((e = stage(ctx, ci.data(), ci.size() * sizeof(CondItem), &dci))) return fail(e);
-        int amax = 0;
-        for (const CondItem& c : ci) amax = std::max(amax, c.A);
-        dim3 gl((amax + 255) / 256, (unsigned)ci.size());
-        cond_L_kernel<<<gl, 256, 0, ctx->stream>>>((const CondItem*)dci, M);
-        cond_update_kernel<<<(unsigned)((entries + 255) / 256), 256, 0, ctx->stream>>>((const CondItem*)dci,
-                                                                                       (int)ci.size(), entries, M);
-        count_launch(ctx, 2);
-        if ((e = check_cuda(ctx, cudaGetLastError(), "conditioning"))) return fail(e);
-      }
-    }
-    std::vector<int> next;
-    for (int t : wave) {
-      if (status[t] == 1) {
-        uint8_t* row = patterns + (size_t)tr[t].sample * M;
-        memset(row, 0, M);
-        for (int c : S[t]) row[c] = 1;
-      } else if (status[t] == 2) {
-        stt.rejections++;
-        if (tr[t].attempt + 1 < max_attempts) {
-          tr[t].attempt++;
-          status[t] = 0;
-          next.push_back(t);
-        }
-      }
-    }
-    wave.swap(next);
+    if (!any) break;
+    if ((e = sampler_advance(ctx, ptrs, prec, stt))) return fail(e);
   }
   if ((e = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync"))) return fail(e);
   dev_free(ctx, work);
+  bool all = true;
+  for (int t = 0; t < T; ++t) {
+    if (tr[t].state == Trajectory::kDone) {
+      uint8_t* row = patterns + (size_t)t * M;
+      memset(row, 0, M);
+      for (int c : tr[t].S) row[c] = 1;
+      if (p0_out) memcpy(p0_out + (size_t)t * M, tr[t].p0.data(), M * sizeof(double));
+    } else {
+      all = false;
+    }
+  }
   stt.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   stt.cond_seconds = stt.seconds - stt.tree_seconds[0] - stt.tree_seconds[1] - stt.tree_seconds[2];
   if (stats) *stats = stt;
-  for (int t = 0; t < T; ++t)
-    if (status[t] != 1) return set_error(ctx, GBS_EREJECT, "postselection attempts exhausted for some samples");
+  if (!all) return set_error(ctx, GBS_EREJECT, "postselection attempts exhausted for some samples");
   return GBS_OK;
 }
