@@ -182,6 +182,109 @@ def sampler_block(ctx, gbs, gi, n_traj, ws, local):
                         "click positions; no-click probability at every one of the 800 steps" % n_traj}
 
 
+def batched_block(ctx, gbs, gi, n_req, n_err):
+    """Uneven probability requests (N ~ U{8..22}, M ~ U{100, 200, 400}, r ~ U[0.4, 1.0],
+    eta ~ U[0.25, 1.0], Haar unitary seeded per request) evaluated as one batch in FP64 and
+    one at a time; plus the FP32 error study on a subsample against certified values."""
+    reqs = gi.batched_requests(4096)[:n_req]
+    t0 = time.perf_counter()
+    states = [gbs.build_state(ctx, gi.haar_unitary(q.M, q.seed), np.full(q.M, q.r), q.eta) for q in reqs]
+    t_inputs = time.perf_counter() - t0
+    pats = [q.modes for q in reqs]
+    terms = float(sum(2 ** q.N for q in reqs))
+    gbs.torontonian_batch(ctx, states[:64], pats[:64], "fp64", "real", check=False)
+    l0 = ctx.launch_count
+    t0 = time.perf_counter()
+    batch = gbs.torontonian_batch(ctx, states, pats, "fp64", "real", check=False)
+    t_batch = time.perf_counter() - t0
+    launches = ctx.launch_count - l0
+    t0 = time.perf_counter()
+    for st, pat in zip(states, pats):
+        gbs.torontonian(ctx, st, pat, "fp64", "real")
+    t_single = time.perf_counter() - t0
+    # FP32 error study: relative error of FP32 and FP64 terms against the certified (AUTO) value
+    idx = list(range(0, n_req, max(1, n_req // n_err)))[:n_err]
+    sub_s, sub_p = [states[i] for i in idx], [pats[i] for i in idx]
+    ref = gbs.torontonian_batch(ctx, sub_s, sub_p, "auto", "real", check=False)
+    f32 = gbs.torontonian_batch(ctx, sub_s, sub_p, "fp32", "real", check=False)
+    by_n = {}
+    for i, r_, a, b in zip(idx, ref, f32, [batch[i] for i in idx]):
+        e32 = abs(a.p - r_.p) / abs(r_.p) if r_.p else float("inf")
+        e64 = abs(b.p - r_.p) / abs(r_.p) if r_.p else float("inf")
+        by_n.setdefault(reqs[i].N, []).append((e32, e64, r_.kappa))
+    err = {int(n): {"fp32_median_rel_err": float(np.median([x[0] for x in v])),
+                    "fp64_median_rel_err": float(np.median([x[1] for x in v])),
+                    "kappa_median": float(np.median([x[2] for x in v])), "count": len(v)}
+           for n, v in sorted(by_n.items())}
+    for st in states:
+        st.free()
+    return {"metric": "batched Torontonians (FP64, uneven N)", "requests": n_req, "subset_terms": terms,
+            "batch_seconds": t_batch, "batch_requests_per_s": n_req / t_batch, "batch_terms_per_s": terms / t_batch,
+            "one_at_a_time_seconds": t_single, "one_at_a_time_requests_per_s": n_req / t_single,
+            "speedup_vs_one_at_a_time": t_single / t_batch, "batch_gpu_launches": launches,
+            "input_seconds": t_inputs, "fp32_error_study": err,
+            "workload": "the first %d of 4096 requests: N~U{8..22}, M~U{100,200,400}, r~U[0.4,1.0], "
+                        "eta~U[0.25,1.0], Haar seeded per request" % n_req}
+
+
+def served_block(ctx, gbs, gi, n_req, max_attempts):
+    """The served dense-subgraph stream: Poisson arrivals (200/s) of postselected sampling jobs on
+    graph-encoded states; latency percentiles of the request loop beside the same requests served
+    one at a time by direct calls (whose results must be identical)."""
+    arrivals, reqs, graphs = gi.served_stream_workload(n_req)
+    cache = {}
+    sts = []
+    for g, eta, N in reqs:
+        if (g, eta, N) not in cache:
+            sp = gi.graph_state(graphs[g], 2.0 * N, eta)
+            cache[(g, eta, N)] = gbs.build_state(ctx, sp.U, sp.r, sp.eta)
+        sts.append(cache[(g, eta, N)])
+    srv = gbs.Server(ctx, arena_bytes=8 << 30, max_active=64)
+    t0 = time.perf_counter()
+    tickets = []
+    for i, (a, (g, eta, N)) in enumerate(zip(arrivals, reqs)):
+        dt = t0 + a - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit_sample(sts[i], seed=1000 + i, sample_index=0, N_post=N, max_attempts=max_attempts))
+    res = [srv.poll(t, timeout_s=1800) for t in tickets]
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.stop()
+    lat = np.array([r["latency_s"] for r in res])
+    ok = sum(1 for r in res if r["status"] == 0)
+    # the same requests, one at a time, in arrival order (single queue)
+    svc = []
+    same = True
+    for i, (g, eta, N) in enumerate(reqs):
+        t1 = time.perf_counter()
+        pats, _, _, status = gbs.sample(ctx, sts[i], 1, seed=1000 + i, N_post=N, max_attempts=max_attempts,
+                                        check=False)
+        svc.append(time.perf_counter() - t1)
+        if status == 0:
+            same &= res[i]["status"] == 0 and res[i]["clicks"] == np.nonzero(pats[0])[0].tolist()
+        else:
+            same &= res[i]["status"] != 0
+    free_at, lat1 = 0.0, []
+    for a, sv in zip(arrivals, svc):
+        start = max(a, free_at)
+        free_at = start + sv
+        lat1.append(free_at - a)
+    lat1 = np.array(lat1)
+    for st in cache.values():
+        st.free()
+    return {"metric": "served p50/p99", "requests": n_req, "accepted_samples": ok,
+            "samples_per_s": ok / wall, "wall_seconds": wall,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "loop_busy_fraction": stats["busy_s"] / max(stats["wall_s"], 1e-9),
+            "one_at_a_time": {"samples_per_s": ok / max(free_at, 1e-9), "p50_s": float(np.percentile(lat1, 50)),
+                              "p99_s": float(np.percentile(lat1, 99)), "busy_seconds": float(sum(svc))},
+            "results_identical_to_one_at_a_time": bool(same),
+            "workload": "Poisson arrivals at 200/s; ER graphs n in [100,200] p=0.1 with a planted 20-vertex "
+                        "p=0.9 part; c for mean photon number 2N; eta in {1,0.5,0.25}; one sample postselected "
+                        "on N in [8,20] per request, up to %d attempts" % max_attempts}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -225,6 +328,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default="", help="sub_e,d_top,grid_per_sm,level_threads (skips the autotuner)")
     ap.add_argument("--sampler-traj", type=int, default=64, help="forced trajectories of the M=800 sampler run (0: skip)")
+    ap.add_argument("--batched-req", type=int, default=1024, help="requests of the uneven batch (of 4096; 0: skip)")
+    ap.add_argument("--served-req", type=int, default=48, help="requests of the served stream (0: skip)")
+    ap.add_argument("--served-attempts", type=int, default=24, help="postselection attempts per served request")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -357,6 +463,10 @@ def main():
     }
     if args.sampler_traj > 0:
         line["sampler"] = sampler_block(ctx, gbs, gi, args.sampler_traj, ws, local)
+    if args.batched_req > 0:
+        line["batched"] = batched_block(ctx, gbs, gi, args.batched_req, 48)
+    if args.served_req > 0:
+        line["served"] = served_block(ctx, gbs, gi, args.served_req, args.served_attempts)
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()

@@ -220,6 +220,54 @@ def planted_graph(n: int, seed: int, p: float = 0.1, k: int = 20, q: float = 0.9
     return A
 
 
+def graph_state(A: np.ndarray, mean_photons: float, eta: float = 1.0) -> StateParams:
+    """Encode a graph into a GBS state (the encoding the paper uses for dense subgraphs, Sec. IV,
+    after its Ref. on GBS and graphs): Takagi factorisation c A = U diag(tanh r) U^T of the scaled
+    adjacency matrix, with c chosen by bisection so that the mean photon number sum_j sinh^2 r_j
+    equals mean_photons, then uniform loss eta.
+
+    For real symmetric A = O diag(mu) O^T the Takagi factors are lambda = |mu| and U = O diag(phase),
+    phase_j = 1 (mu_j >= 0) or i (mu_j < 0), so that U diag(lambda) U^T = A.
+    """
+    mu, O = np.linalg.eigh(np.asarray(A, dtype=np.float64))
+    lam = np.abs(mu)
+    U = O * np.where(mu >= 0, 1.0, 1j)[None, :]
+    lmax = lam.max()
+
+    def nbar(c):
+        t = c * lam
+        return float(np.sum(t * t / (1.0 - t * t)))
+
+    lo, hi = 0.0, (1.0 - 1e-12) / lmax
+    if nbar(hi) < mean_photons:
+        raise ValueError("mean photon number out of reach for this graph")
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if nbar(mid) < mean_photons:
+            lo = mid
+        else:
+            hi = mid
+    c = 0.5 * (lo + hi)
+    return StateParams(np.ascontiguousarray(U), np.arctanh(c * lam), float(eta))
+
+
+def served_stream_workload(n_req: int, seed: int = 5, rate_hz: float = 200.0, n_graphs: int = 4):
+    """Requests of the served dense-subgraph stream: Poisson arrival times, and per request a
+    graph (Erdos-Renyi n in [100, 200], p = 0.1, planted 20-vertex part at p = 0.9), a loss
+    eta in {1, 0.5, 0.25} and a postselected click count N in [8, 20]; the state of request
+    (graph, eta, N) has mean photon number 2N.  Returns (arrivals, [(graph, eta, N)], graphs)."""
+    s = stream_seed(seed, "requests")
+    u = uniforms(s, 0, 3 * n_req + n_graphs).reshape(-1)
+    graphs = [planted_graph(100 + int(u[3 * n_req + g] * 101), seed * 97 + g) for g in range(n_graphs)]
+    reqs = []
+    for i in range(n_req):
+        g = int(u[3 * i] * n_graphs)
+        eta = (1.0, 0.5, 0.25)[int(u[3 * i + 1] * 3)]
+        N = 8 + int(u[3 * i + 2] * 13)
+        reqs.append((g, eta, N))
+    return poisson_arrivals(rate_hz, n_req, seed), reqs, graphs
+
+
 def poisson_arrivals(rate_hz: float, n: int, seed: int) -> np.ndarray:
     """Arrival times (seconds) of a Poisson process of the given rate."""
     u = uniforms(stream_seed(seed, "arrivals"), 0, n)

@@ -124,7 +124,9 @@ gbs_status gbs_measure_fp64_peak(gbs_ctx* ctx, double* gflops);
  *   V = S S^+ / 2,  S = [[U ch R, U sh R], [U* sh R, U* ch R]],  R = diag(r),
  *   then V <- eta V + (1 - eta) I/2.
  * V_out (may be NULL): caller-owned 2M x 2M complex, receives V in block order.
- * *st receives a library-owned handle keeping U, r, eta and V on the device.
+ * *st receives a library-owned handle keeping U, r, eta on the device (16 M^2
+ * bytes); V itself (64 M^2 bytes) is built on the device when first needed
+ * (V_out, sampling).
  * Errors: GBS_EINVAL (M < 1, eta outside (0, 1], non-finite input),
  * GBS_ENOMEM, GBS_ECUDA. */
 gbs_status gbs_build_state(gbs_ctx* ctx, int M, const double* U, const double* r, double eta, double* V_out,

@@ -87,7 +87,7 @@ struct gbs_state {
   gbs::DevBuf r;      // M doubles
   gbs::DevBuf alpha;  // M doubles: (1/d+ + 1/d-)/2
   gbs::DevBuf beta;   // M doubles: (1/d+ - 1/d-)/2
-  gbs::DevBuf V;      // 2M x 2M complex covariance, block order (a, a^+)
+  gbs::DevBuf V;      // 2M x 2M complex covariance, block order (a, a^+); built on first use
   gbs::DevBuf Sinv;   // 2M x 2M complex Sigma^-1 (states given by V only)
   gbs::DevBuf sig_real;  // 2M x 2M Sigma in the real x/p basis (built by the first gbs_sample)
 };
@@ -176,6 +176,8 @@ void server_shutdown(gbs_ctx* ctx);
 gbs_status state_build(gbs_ctx* ctx, int M, const double* U, const double* r, double eta, double* V_out,
                        gbs_state** out);
 gbs_status state_from_V(gbs_ctx* ctx, int M, const double* V, gbs_state** out);
+// Build the covariance V of a factor-built state if it is not there yet.
+gbs_status ensure_V(gbs_ctx* ctx, gbs_state* st);
 // Enqueue the packed lower triangle of (Sigma^-1)_S (FP64; complex entries as
 // (re, im) pairs, or real x/p entries) into dev_out on the context stream.
 gbs_status click_block(gbs_ctx* ctx, const gbs_state* st, const int* modes, int N, int real_basis, void* dev_out);

@@ -240,6 +240,7 @@ gbs_status ensure_sigma_real(gbs_ctx* ctx, gbs_state* st) {
   if (st->sig_real.ptr) return GBS_OK;
   const long long M = st->M;
   gbs_status e;
+  if ((e = ensure_V(ctx, st))) return e;
   if ((e = dev_alloc(ctx, st->sig_real, (size_t)(4 * M * M) * sizeof(double)))) return e;
   sigma_real_kernel<<<(unsigned)((M * M + 255) / 256), 256, 0, ctx->stream>>>((const cplx<double>*)st->V.ptr,
                                                                               (int)M, (double*)st->sig_real.ptr);

@@ -217,6 +217,37 @@ static gbs_status alloc_state(gbs_ctx* ctx, int M, gbs_state** out) {
   return GBS_OK;
 }
 
+// The covariance V of a factor-built state, on first use (sampling, V_out).
+gbs_status ensure_V(gbs_ctx* ctx, gbs_state* st) {
+  if (st->V.ptr) return GBS_OK;
+  const int M = st->M;
+  const size_t MM = (size_t)M * M;
+  DevBuf tmp;
+  gbs_status e;
+  if ((e = dev_alloc(ctx, st->V, 4 * MM * 16)) || (e = dev_alloc(ctx, tmp, (3 * (size_t)M + 1) * 8))) {
+    dev_free(ctx, tmp);
+    return e;
+  }
+  double* ch2 = (double*)tmp.ptr;
+  double* sh2 = ch2 + M;
+  double* logd = sh2 + M;
+  cudaStream_t s = ctx->stream;
+  // alpha/beta are already in place: rewrite them with identical values
+  state_params_kernel<<<(M + 127) / 128, 128, 0, s>>>((const double*)st->r.ptr, st->eta, M, (double*)st->alpha.ptr,
+                                                      (double*)st->beta.ptr, ch2, sh2, logd);
+  const long long nt = (long long)M * M;
+  build_V_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>((const cplx<double>*)st->U.ptr, ch2, sh2, st->eta, M,
+                                                                (cplx<double>*)st->V.ptr);
+  count_launch(ctx, 2);
+  if ((e = check_cuda(ctx, cudaGetLastError(), "build V")) ||
+      (e = check_cuda(ctx, cudaStreamSynchronize(s), "sync"))) {
+    dev_free(ctx, tmp);
+    return e;
+  }
+  dev_free(ctx, tmp);
+  return GBS_OK;
+}
+
 gbs_status state_build(gbs_ctx* ctx, int M, const double* U, const double* r, double eta, double* V_out,
                        gbs_state** out) {
   if (M < 1 || !U || !r || !out) return set_error(ctx, GBS_EINVAL, "gbs_build_state: bad arguments");
@@ -239,7 +270,7 @@ gbs_status state_build(gbs_ctx* ctx, int M, const double* U, const double* r, do
   };
   if ((e = dev_alloc(ctx, st->U, MM * 16)) || (e = dev_alloc(ctx, st->r, M * 8)) ||
       (e = dev_alloc(ctx, st->alpha, M * 8)) || (e = dev_alloc(ctx, st->beta, M * 8)) ||
-      (e = dev_alloc(ctx, st->V, 4 * MM * 16)) || (e = dev_alloc(ctx, tmp, (3 * (size_t)M + 1) * 8)))
+      (e = dev_alloc(ctx, tmp, (3 * (size_t)M + 1) * 8)))
     return fail(e);
   cudaStream_t s = ctx->stream;
   if ((e = check_cuda(ctx, cudaMemcpyAsync(st->U.ptr, U, MM * 16, cudaMemcpyHostToDevice, s), "copy U")) ||
@@ -252,18 +283,17 @@ gbs_status state_build(gbs_ctx* ctx, int M, const double* U, const double* r, do
   state_params_kernel<<<(M + 127) / 128, 128, 0, s>>>((const double*)st->r.ptr, eta, M, (double*)st->alpha.ptr,
                                                       (double*)st->beta.ptr, ch2, sh2, logd);
   sum_dd_kernel<<<1, 256, 0, s>>>(logd, M, ld_out);
-  const long long nt = (long long)M * M;
-  build_V_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>((const cplx<double>*)st->U.ptr, ch2, sh2, eta, M,
-                                                                (cplx<double>*)st->V.ptr);
-  count_launch(ctx, 3);
+  count_launch(ctx, 2);
   if ((e = check_cuda(ctx, cudaGetLastError(), "state kernels"))) return fail(e);
   if ((e = check_cuda(ctx, cudaMemcpyAsync(&st->logdet_sigma, ld_out, 8, cudaMemcpyDeviceToHost, s), "copy logdet")))
     return fail(e);
-  if (V_out &&
-      (e = check_cuda(ctx, cudaMemcpyAsync(V_out, st->V.ptr, 4 * MM * 16, cudaMemcpyDeviceToHost, s), "copy V")))
-    return fail(e);
   if ((e = check_cuda(ctx, cudaStreamSynchronize(s), "sync"))) return fail(e);
   dev_free(ctx, tmp);
+  if (V_out) {
+    if ((e = ensure_V(ctx, st))) return fail(e);
+    if ((e = check_cuda(ctx, cudaMemcpy(V_out, st->V.ptr, 4 * MM * 16, cudaMemcpyDeviceToHost), "copy V")))
+      return fail(e);
+  }
   *out = st;
   return GBS_OK;
 }
