@@ -173,7 +173,8 @@ def sampler_block(ctx, gbs, gi, n_traj, ws, local):
     st.free()
     return {"metric": "M=800,N=20 samples/s", "value": ws * n_traj / dt, "unit": "samples/s",
             "seconds": dt, "trajectories": n_traj, "steps_evaluated": stats["steps"],
-            "escalations": stats["escalations"], "gpu_launches": ctx.launch_count - l0,
+            "escalations": stats["escalations"], "uncertified_steps": stats["uncertified"],
+            "gpu_launches": ctx.launch_count - l0,
             "trees_fp64_dd_td": stats["trees"], "tree_seconds_fp64_dd_td": stats["tree_seconds"],
             "other_seconds": stats["cond_seconds"], "dd_tuning": ctx.tuning("dd", "real"),
             "td_tuning": ctx.tuning("td", "real"),

@@ -186,6 +186,7 @@ typedef struct {
   long long trees[3];     /* subset trees evaluated in FP64, DD, TD */
   double tree_seconds[3]; /* wall time spent in those tree batches */
   double cond_seconds;    /* wall time of gathers, decisions and conditioning */
+  long long uncertified;  /* steps whose p0 error bound stayed above 5e-10 even in TD */
 } gbs_sample_stats;
 
 /* Chain-rule threshold-detector samples (the paper's Sec. II algorithm in

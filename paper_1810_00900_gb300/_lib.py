@@ -44,7 +44,7 @@ class gbs_sample_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("escalations", ctypes.c_longlong),
                 ("near_ties", ctypes.c_longlong), ("rejections", ctypes.c_longlong), ("seconds", ctypes.c_double),
                 ("trees", ctypes.c_longlong * 3), ("tree_seconds", ctypes.c_double * 3),
-                ("cond_seconds", ctypes.c_double)]
+                ("cond_seconds", ctypes.c_double), ("uncertified", ctypes.c_longlong)]
 
 
 class gbs_request(ctypes.Structure):

@@ -384,6 +384,7 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
         const double p0 = exc > 0 ? inc / exc : INFINITY;
         dp = 4.0 * n * u * q.res.abs_sum * (1.0 + p0) / std::max(exc, 1e-300);
       }
+      if (!(dp < TOL) && (prec != GBS_PREC_AUTO || (q.prec == GBS_PREC_TD && !q.half))) stt.uncertified++;
       if (prec == GBS_PREC_AUTO && !(dp < TOL) && !(q.prec == GBS_PREC_TD && !q.half)) {
         q.half = 0;
         q.n = q.tj->m + 1;
