@@ -47,10 +47,10 @@ def tree_flops(q: int, complex_basis: bool) -> int:
     counted from the kernel's formulation: an FMA counts 2, a multiply, add or
     inverse square root 1.  Per included pivot: det P, rsqrt, the scaled inverse,
     L = u P^-1 for each of the 2q-2 rows below, and the rank-2 update of the
-    lower triangle of the (2q-2)^2 Schur complement.  Leaves add their term to
-    three accumulators."""
+    lower triangle of the (2q-2)^2 Schur complement.  A last-level node adds
+    its two leaf terms to the sums (s*g by one FMA, s by one add)."""
     if q == 1:
-        return 11 if complex_basis else 9
+        return 9 if complex_basis else 7
     d = 2 * q - 2
     if complex_basis:
         node = 12 + 20 * d + 16 * (sym(d) - d) + 8 * d

@@ -215,13 +215,7 @@ __global__ void __launch_bounds__(128) batch_leaf_kernel(const LeafSeg* __restri
 #pragma unroll
       for (int e = 0; e < sym(2 * Q); ++e) c[e] = nodes[(long long)e * sg.count + node];
       const T s = (sg.buf ? s1 : s0)[sg.s_base + node];
-      Acc ai = from_double<Acc>(0.0), ae = from_double<Acc>(0.0), aa = from_double<Acc>(0.0);
-      bool bad = false;
-      Dfs<E, Q, 2 * Q, 0, false>::run(c, s, ai, ae, aa, bad);
-      if (bad) atomicExch(status + sg.tree, (int)kStatusNotPD);
-      inc = to_red(ai, (Red*)nullptr);
-      exc = to_red(ae, (Red*)nullptr);
-      asum = to_double(aa);
+      if (!subtree_sums<E, Q>(c, s, inc, exc, asum)) atomicExch(status + sg.tree, (int)kStatusNotPD);
       if ((sg.depth - __popcll((unsigned long long)node)) & 1) {
         inc = red_neg(inc);
         exc = red_neg(exc);
@@ -328,13 +322,7 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
 #pragma unroll
       for (int e = 0; e < sym(2 * Q); ++e) c[e] = src[e * nodes + t];
       const T sv = ssrc[t];
-      Acc ai = from_double<Acc>(0.0), ae = from_double<Acc>(0.0), aa = from_double<Acc>(0.0);
-      bool bad2 = false;
-      Dfs<E, Q, 2 * Q, 0, false>::run(c, sv, ai, ae, aa, bad2);
-      if (bad2) atomicExch(status + sg.tree, (int)kStatusNotPD);
-      inc = to_red(ai, (Red*)nullptr);
-      exc = to_red(ae, (Red*)nullptr);
-      asum = to_double(aa);
+      if (!subtree_sums<E, Q>(c, sv, inc, exc, asum)) atomicExch(status + sg.tree, (int)kStatusNotPD);
       const unsigned long long gnode = ((unsigned long long)root << sg.e_levels) | (unsigned long long)t;
       if ((sg.depth_leaf - __popcll(gnode)) & 1) {
         inc = red_neg(inc);

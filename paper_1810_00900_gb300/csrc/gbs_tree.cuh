@@ -74,6 +74,33 @@ GBS_HD void acc_sub(double& a, float x) { a -= (double)x; }
 GBS_HD void acc_sub(dd& a, const dd& x) { a = a - x; }
 GBS_HD void acc_sub(td& a, const td& x) { a = a - x; }
 
+// acc += a * b (the term s * g of an included leaf)
+GBS_HD void acc_fpa(double& acc, double a, double b) { acc = fma(a, b, acc); }
+GBS_HD void acc_fpa(double& acc, float a, float b) { acc += (double)(a * b); }
+GBS_HD void acc_fpa(dd& acc, const dd& a, const dd& b) { acc = acc + a * b; }
+GBS_HD void acc_fpa(td& acc, const td& a, const td& b) { acc = acc + a * b; }
+
+// Per-thread term sums split by sign: no sum cancels inside a thread, each
+// leaf pair costs two accumulations, and the absolute sum comes for free:
+// f_inc = ip - in, f_exc = ep - en, abs = ip + in + ep + en.
+template <class Acc>
+struct Sums {
+  Acc ip, in, ep, en;
+};
+template <class Acc>
+GBS_HD Sums<Acc> sums_zero() {
+  const Acc z = from_double<Acc>(0.0);
+  return Sums<Acc>{z, z, z, z};
+}
+
+// A pivot determinant that is not positive: the floating types need no test
+// on the hot path (the inverse square root of a value <= 0 is NaN or inf and
+// reaches the sums, which are checked once per thread).
+GBS_HD bool not_positive(double) { return false; }
+GBS_HD bool not_positive(float) { return false; }
+GBS_HD bool not_positive(const dd&) { return false; }
+GBS_HD bool not_positive(const td&) { return false; }
+
 GBS_HD dd to_red(double a, dd*) { return dd_make(a); }
 GBS_HD dd to_red(const dd& a, dd*) { return a; }
 GBS_HD td to_red(const td& a, td*) { return a; }
@@ -171,20 +198,16 @@ template <class E, int Q, int D, int OFF, bool NEG>
 struct Dfs {
   typedef typename real_of<E>::type T;
   typedef typename acc_traits<T>::Acc Acc;
-  static __device__ __forceinline__ void run(const E (&c)[sym(D)], const T& s, Acc& inc, Acc& exc, Acc& asum,
-                                             bool& bad) {
+  static __device__ __forceinline__ void run(const E (&c)[sym(D)], const T& s, Sums<Acc>& acc, bool& bad) {
     const T p00 = re_of(c[tri(OFF, OFF)]);
     const T p11 = re_of(c[tri(OFF + 1, OFF + 1)]);
     const E p10 = c[tri(OFF + 1, OFF)];
     const T det = p00 * p11 - norm2(p10);
-    bad |= !(to_double(det) > 0.0);
+    bad |= not_positive(det);
     const T g = rsqrt_(det);
     if constexpr (Q == 1) {
-      const T sg = s * g;
-      // include leaf: sign (-1)^NEG; exclude leaf: one more exclusion
-      if (NEG) { acc_sub(inc, sg); acc_add(exc, s); } else { acc_add(inc, sg); acc_sub(exc, s); }
-      acc_add(asum, sg);
-      acc_add(asum, s);
+      // include leaf s*g with sign (-1)^NEG; exclude leaf s with one more exclusion
+      if (NEG) { acc_fpa(acc.in, s, g); acc_add(acc.ep, s); } else { acc_fpa(acc.ip, s, g); acc_add(acc.en, s); }
     } else {
       constexpr int DN = 2 * Q - 2;
       E cn[sym(DN)];
@@ -204,11 +227,35 @@ struct Dfs {
         E v = fms_conj_re(c[tri(OFF + 2 + a, OFF + 2 + a)], L0, u0);
         cn[tri(a, a)] = fms_conj_re(v, L1, u1);
       }
-      Dfs<E, Q - 1, DN, 0, NEG>::run(cn, s * g, inc, exc, asum, bad);
-      Dfs<E, Q - 1, D, OFF + 2, !NEG>::run(c, s, inc, exc, asum, bad);
+      Dfs<E, Q - 1, DN, 0, NEG>::run(cn, s * g, acc, bad);
+      Dfs<E, Q - 1, D, OFF + 2, !NEG>::run(c, s, acc, bad);
     }
   }
 };
+
+// Register subtree of one node (all Q levels below it): the node's signed sums
+// as reduction values and its absolute sum; returns false if a pivot was not
+// positive definite (the sums then carry NaN or inf, or the type flagged it).
+GBS_HD dd red_diff(double a, double b, dd*) {
+  dd r;
+  two_sum(a, -b, r.hi, r.lo);
+  return r;
+}
+GBS_HD dd red_diff(const dd& a, const dd& b, dd*) { return a - b; }
+GBS_HD td red_diff(const td& a, const td& b, td*) { return a - b; }
+
+template <class E, int Q, class Red>
+__device__ __forceinline__ bool subtree_sums(const E (&c)[sym(2 * Q)], const typename real_of<E>::type& s, Red& inc,
+                                             Red& exc, double& asum) {
+  typedef typename acc_traits<typename real_of<E>::type>::Acc Acc;
+  Sums<Acc> a = sums_zero<Acc>();
+  bool bad = false;
+  Dfs<E, Q, 2 * Q, 0, false>::run(c, s, a, bad);
+  inc = red_diff(a.ip, a.in, (Red*)nullptr);
+  exc = red_diff(a.ep, a.en, (Red*)nullptr);
+  asum = to_double(a.ip) + to_double(a.in) + (to_double(a.ep) + to_double(a.en));
+  return !bad && isfinite(asum);
+}
 
 template <class Red>
 __device__ __forceinline__ void block_reduce_store(Red inc, Red exc, double asum, Partial<Red>* out) {
@@ -250,13 +297,7 @@ __global__ void __launch_bounds__(128) tree_leaf_kernel(const E* __restrict__ no
 #pragma unroll
     for (int e = 0; e < sym(2 * Q); ++e) c[e] = nodes[(long long)e * count + node];
     const T s = snode[node];
-    Acc ai = from_double<Acc>(0.0), ae = from_double<Acc>(0.0), aa = from_double<Acc>(0.0);
-    bool bad = false;
-    Dfs<E, Q, 2 * Q, 0, false>::run(c, s, ai, ae, aa, bad);
-    if (bad) atomicExch(status, (int)kStatusNotPD);
-    inc = to_red(ai, (Red*)nullptr);
-    exc = to_red(ae, (Red*)nullptr);
-    asum = to_double(aa);
+    if (!subtree_sums<E, Q>(c, s, inc, exc, asum)) atomicExch(status, (int)kStatusNotPD);
     // sign of the node: (-1)^(exclusions above) = (-1)^(depth - popcount(node))
     if ((depth - __popcll((unsigned long long)node)) & 1) { inc = red_neg(inc); exc = red_neg(exc); }
   }
