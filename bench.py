@@ -161,7 +161,7 @@ def sampler_block(ctx, gbs, gi, n_traj, ws, local):
     (the paper's forced-outcome benchmark); p0 is evaluated at all 800 steps of every trajectory."""
     stp, clicks = gi.chain_sampling_workload(800, 20, n_traj, seed=2)
     st = gbs.build_state(ctx, stp.U, stp.r, stp.eta)
-    ctx.autotune("dd", "real", 18)
+    ctx.autotune("fx", "real", 18)
     ctx.autotune("td", "real", 18)
     forced = np.array(clicks, dtype=np.int32)
     gbs.sample(ctx, st, 2, seed=2, N_post=20, forced_clicks=forced[:2])  # warm-up
@@ -175,12 +175,36 @@ def sampler_block(ctx, gbs, gi, n_traj, ws, local):
             "seconds": dt, "trajectories": n_traj, "steps_evaluated": stats["steps"],
             "escalations": stats["escalations"], "uncertified_steps": stats["uncertified"],
             "gpu_launches": ctx.launch_count - l0,
-            "trees_fp64_dd_td": stats["trees"], "tree_seconds_fp64_dd_td": stats["tree_seconds"],
-            "other_seconds": stats["cond_seconds"], "dd_tuning": ctx.tuning("dd", "real"),
+            "trees_fp64_dd_td_fx": stats["trees"], "tree_seconds_fp64_dd_td_fx": stats["tree_seconds"],
+            "other_seconds": stats["cond_seconds"], "fx_tuning": ctx.tuning("fx", "real"),
             "td_tuning": ctx.tuning("td", "real"),
             "p0_range": [float(p0.min()), float(p0.max())], "status": status,
             "workload": "M=800 modes, r~U[0.3,0.9], Haar seed 2, eta=1; %d forced trajectories with 20 uniform "
                         "click positions; no-click probability at every one of the 800 steps" % n_traj}
+
+
+def walltime_block(ctx, gbs, gi, ms):
+    """One worst-case sample per click count m at the paper's Table II sizes (l modes,
+    8 dB, all m clicks first), AUTO precision; the paper's Titan walltimes beside it as
+    context (hours on the quoted node counts, quad precision)."""
+    paper = {10: (0.11, 1), 12: (0.68, 4), 14: (0.97, 32), 16: (1.98, 128), 18: (1.90, 1024), 20: (1.83, 8192)}
+    rows = []
+    for m in ms:
+        stp, clicks = gi.walltime_workload(m)
+        st = gbs.build_state(ctx, stp.U, stp.r, stp.eta)
+        forced = np.asarray(clicks, dtype=np.int32)[None, :]
+        t0 = time.perf_counter()
+        pats, p0, stats, status = gbs.sample(ctx, st, 1, seed=m, N_post=m, forced_clicks=forced, want_p0=True)
+        dt = time.perf_counter() - t0
+        st.free()
+        rows.append({"m": m, "modes": int(stp.U.shape[0]), "seconds_per_sample": dt, "status": status,
+                     "trees_fp64_dd_td_fx": stats["trees"], "tree_seconds_fp64_dd_td_fx": stats["tree_seconds"],
+                     "escalations": stats["escalations"], "uncertified_steps": stats["uncertified"],
+                     "p0_min": float(p0.min()),
+                     "paper_titan_hours": paper[m][0], "paper_titan_nodes": paper[m][1]})
+    return {"metric": "seconds per worst-case sample (paper Table II sizes)", "rows": rows,
+            "workload": "l in {200,288,392,512,624,800} modes for m in {10..20} clicks, 8 dB squeezing, Haar, "
+                        "no loss; the m clicks forced on the first m measured modes"}
 
 
 def batched_block(ctx, gbs, gi, n_req, n_err):
@@ -332,6 +356,8 @@ def main():
     ap.add_argument("--batched-req", type=int, default=1024, help="requests of the uneven batch (of 4096; 0: skip)")
     ap.add_argument("--served-req", type=int, default=48, help="requests of the served stream (0: skip)")
     ap.add_argument("--served-attempts", type=int, default=24, help="postselection attempts per served request")
+    ap.add_argument("--walltime-m", default="10,12,14,16,18,20",
+                    help="click counts of the worst-case walltime rows (paper Table II sizes; empty: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -468,6 +494,8 @@ def main():
         line["batched"] = batched_block(ctx, gbs, gi, args.batched_req, 48)
     if args.served_req > 0:
         line["served"] = served_block(ctx, gbs, gi, args.served_req, args.served_attempts)
+    if args.walltime_m:
+        line["walltime"] = walltime_block(ctx, gbs, gi, [int(x) for x in args.walltime_m.split(",")])
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()

@@ -167,6 +167,20 @@ def single_large_torontonian_workload(N: int = 24):
     return st, random_modes(200, N, seed=1)
 
 
+# Mode counts of the paper's walltime benchmark (Table II): l modes for m clicks.
+WALLTIME_MODES = {10: 200, 12: 288, 14: 392, 16: 512, 18: 624, 20: 800}
+
+
+def walltime_workload(m: int, seed: int = 10):
+    """The paper's walltime benchmark (Sec. III B, Table II) for m clicks: l modes
+    (WALLTIME_MODES), 8 dB squeezing in every mode, Haar unitary (seed + m), no loss,
+    and the worst-case click positions -- the first m measured modes (l-1 .. l-m, the
+    measurement runs from the last mode down) -- as forced outcomes."""
+    M = WALLTIME_MODES[m]
+    st = StateParams(haar_unitary(M, seed + m), np.full(M, db_to_r(8.0)), 1.0)
+    return st, np.arange(M - 1, M - 1 - m, -1, dtype=np.int64)
+
+
 def chain_sampling_workload(M: int = 800, n_clicks: int = 20, n_traj: int = 64, seed: int = 2):
     """M modes, r ~ U[0.3, 0.9] per mode, Haar unitary, no loss, plus n_traj forced
     click-position sets of n_clicks modes each (drawn uniformly, the paper's forced-outcome

@@ -1,4 +1,5 @@
 // C ABI entry points: context, memory ledger, states, probabilities.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -73,6 +74,49 @@ static gbs_status validate_modes(gbs_ctx* ctx, const int* modes, int N, int M) {
 gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, const int* const* modes, const int* N,
                        int prec, int basis, double rel_tol, gbs_prob* out);
 
+// Smallest and largest eigenvalue of the symmetric D x D matrix whose lower
+// triangle is G (row-major): cyclic Jacobi rotations on a host copy.  Returns
+// false if they do not converge.
+bool sym_eig_range(const double* G, int D, double& lmin, double& lmax) {
+  std::vector<double> A((size_t)D * D);
+  for (int a = 0; a < D; ++a)
+    for (int b = 0; b <= a; ++b) A[(size_t)a * D + b] = A[(size_t)b * D + a] = G[(size_t)a * D + b];
+  for (int sweep = 0;; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int a = 0; a < D; ++a) {
+      diag += A[(size_t)a * D + a] * A[(size_t)a * D + a];
+      for (int b = 0; b < a; ++b) off += A[(size_t)a * D + b] * A[(size_t)a * D + b];
+    }
+    if (off <= 1e-30 * diag) break;
+    if (sweep == 60) return false;
+    for (int p = 0; p < D; ++p)
+      for (int q = p + 1; q < D; ++q) {
+        const double apq = A[(size_t)p * D + q];
+        if (apq == 0.0) continue;
+        // rotation zeroing A[p][q]: tan of the angle is the smaller root of t^2 + 2 theta t - 1
+        const double theta = (A[(size_t)q * D + q] - A[(size_t)p * D + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < D; ++k) {
+          const double akp = A[(size_t)k * D + p], akq = A[(size_t)k * D + q];
+          A[(size_t)k * D + p] = c * akp - sn * akq;
+          A[(size_t)k * D + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < D; ++k) {
+          const double apk = A[(size_t)p * D + k], aqk = A[(size_t)q * D + k];
+          A[(size_t)p * D + k] = c * apk - sn * aqk;
+          A[(size_t)q * D + k] = sn * apk + c * aqk;
+        }
+      }
+  }
+  lmin = lmax = A[0];
+  for (int a = 1; a < D; ++a) {
+    lmin = std::min(lmin, A[(size_t)a * D + a]);
+    lmax = std::max(lmax, A[(size_t)a * D + a]);
+  }
+  return true;
+}
+
 }  // namespace gbs
 
 using namespace gbs;
@@ -126,6 +170,8 @@ gbs_status gbs_ctx_create(gbs_ctx** out, int device, size_t hbm_budget_bytes) {
     ctx->tune[GBS_PREC_DD][b].d_top = 5;
     ctx->tune[GBS_PREC_TD][b].sub_e = 6;
     ctx->tune[GBS_PREC_TD][b].d_top = 4;
+    ctx->tune[GBS_PREC_FX][b].sub_e = 6;
+    ctx->tune[GBS_PREC_FX][b].d_top = 6;
   }
   *out = ctx;
   return GBS_OK;
@@ -254,7 +300,7 @@ gbs_status gbs_torontonian(gbs_ctx* ctx, const gbs_state* st, const int* modes, 
   cudaSetDevice(ctx->device);
   gbs_status e;
   if ((e = validate_modes(ctx, modes, N, st->M))) return e;
-  if (prec < GBS_PREC_AUTO || prec > GBS_PREC_FP32_DIAG) return set_error(ctx, GBS_EINVAL, "bad precision");
+  if (prec < GBS_PREC_AUTO || prec > GBS_PREC_FX) return set_error(ctx, GBS_EINVAL, "bad precision");
   const int* mp[1] = {modes};
   const int Nv[1] = {N};
   return probs_batch(ctx, 1, &st, mp, Nv, prec, basis, rel_tol, out);
@@ -263,10 +309,16 @@ gbs_status gbs_torontonian(gbs_ctx* ctx, const gbs_state* st, const int* modes, 
 gbs_status gbs_subset_sum(gbs_ctx* ctx, int n, const double* G, int basis, int prec, double* inc, double* exc,
                           double* tor, double* abs_sum) {
   if (!ctx || !G || n < 1 || n > 32) return GBS_EINVAL;
-  if (prec < GBS_PREC_FP64 || prec > GBS_PREC_FP32_DIAG) return GBS_EINVAL;
+  if (prec < GBS_PREC_FP64 || prec > GBS_PREC_FX) return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
   cudaSetDevice(ctx->device);
   const bool real = basis != GBS_BASIS_COMPLEX;
+  if (prec == GBS_PREC_FX) {
+    double lmin = 0.0, lmax = 0.0;
+    if (!real || !sym_eig_range(G, 2 * n, lmin, lmax) || !(lmin >= 0x1p-10 && lmax <= 1024.0) ||
+        !(n * std::log2(1.0 + 1.0 / lmin) < 60.0))
+      return set_error(ctx, GBS_EPRECISION, "gbs_subset_sum: matrix outside the fixed-point range");
+  }
   const int D = 2 * n, ne = D * (D + 1) / 2;
   std::vector<double> packed(ne * (real ? 1 : 2));
   for (int a = 0; a < D; ++a)
@@ -287,6 +339,7 @@ gbs_status gbs_subset_sum(gbs_ctx* ctx, int n, const double* G, int basis, int p
   const double zero = 0.0;
   ProbOut r;
   if ((e = batch_eval(ctx, prec, real, 1, &tree, G_dev, &zero, &r))) return e;
+  if (r.status == kStatusRange) return set_error(ctx, GBS_EPRECISION, "a fixed-point tree left its range");
   if (r.status) return set_error(ctx, GBS_ENOTPD, "a pivot block is not positive definite");
   for (int i = 0; i < 3; ++i) {
     if (inc) inc[i] = r.inc[i];

@@ -93,7 +93,7 @@ __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
     const T p00 = re_of(C[tri(o, o)]), p11 = re_of(C[tri(o + 1, o + 1)]);
     const E p10 = C[tri(o + 1, o)];
     const T det = p00 * p11 - norm2(p10);
-    bad |= !(to_double(det) > 0.0);
+    bad |= !is_pos(det);
     const T g = rsqrt_(det);
     const T inv = g * g;
     const T q00 = p00 * inv, q11 = p11 * inv;
@@ -132,7 +132,7 @@ __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
   }
   if (threadIdx.x == 0) {
     sout[sg.s_base + node] = s;
-    if (bad) atomicExch(status + sg.tree, (int)kStatusNotPD);
+    if (bad) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
   }
 }
 
@@ -159,8 +159,8 @@ __global__ void batch_level_kernel(const LevelSeg* __restrict__ segs, int nseg, 
   const T p11 = re_of(PAR(1, 1));
   const E p10 = PAR(1, 0);
   const T det = p00 * p11 - norm2(p10);
-  if (!(to_double(det) > 0.0)) {
-    if (grp == 0) atomicExch(status + sg.tree, (int)kStatusNotPD);
+  if (!is_pos(det)) {
+    if (grp == 0) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
     return;
   }
   const T g = rsqrt_(det);
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(128) batch_leaf_kernel(const LeafSeg* __restri
 #pragma unroll
       for (int e = 0; e < sym(2 * Q); ++e) c[e] = nodes[(long long)e * sg.count + node];
       const T s = (sg.buf ? s1 : s0)[sg.s_base + node];
-      if (!subtree_sums<E, Q>(c, s, inc, exc, asum)) atomicExch(status + sg.tree, (int)kStatusNotPD);
+      if (!subtree_sums<E, Q>(c, s, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
       if ((sg.depth - __popcll((unsigned long long)node)) & 1) {
         inc = red_neg(inc);
         exc = red_neg(exc);
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
         const T p11 = re_of(src[tri(1, 1) * nodes + t]);
         const E p10 = src[tri(1, 0) * nodes + t];
         const T det = p00 * p11 - norm2(p10);
-        bad |= !(to_double(det) > 0.0);
+        bad |= !is_pos(det);
         const T g = rsqrt_(det);
         const T inv = g * g;
         pg[t] = g;
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
       nodes = n2;
       --q;
     }
-    if (bad) atomicExch(status + sg.tree, (int)kStatusNotPD);
+    if (bad) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
     Red inc = red_zero<Red>(), exc = red_zero<Red>();
     double asum = 0.0;
     const int t = threadIdx.x;
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
 #pragma unroll
       for (int e = 0; e < sym(2 * Q); ++e) c[e] = src[e * nodes + t];
       const T sv = ssrc[t];
-      if (!subtree_sums<E, Q>(c, sv, inc, exc, asum)) atomicExch(status + sg.tree, (int)kStatusNotPD);
+      if (!subtree_sums<E, Q>(c, sv, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
       const unsigned long long gnode = ((unsigned long long)root << sg.e_levels) | (unsigned long long)t;
       if ((sg.depth_leaf - __popcll(gnode)) & 1) {
         inc = red_neg(inc);

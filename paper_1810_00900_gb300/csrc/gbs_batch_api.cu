@@ -1,5 +1,6 @@
 // Batched probabilities: staging arena, batched click blocks, per-tree finish,
 // the precision ladder over a batch, and gbs_torontonian_batch.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -44,7 +45,23 @@ gbs_status stage(gbs_ctx* ctx, const void* data, size_t bytes, const void** dev)
 }
 
 const BatchTune& batch_tune_for(gbs_ctx* ctx, int prec, bool real) {
-  return ctx->tune[prec < 0 || prec > 4 ? 1 : prec][real ? 1 : 0];
+  return ctx->tune[prec < 0 || prec > GBS_PREC_FX ? 1 : prec][real ? 1 : 0];
+}
+
+// Every value of a tree over n modes of (Sigma^-1)_S fits the fixed-point
+// range: Sigma >= I/2 bounds the entries by 2, the pivot determinants lie in
+// [1/sigma_max^2, 4], each included pivot multiplies s by at most sigma_max,
+// and the sums are bounded by (1 + sigma_max)^n.
+bool fx_ok_inverse(const gbs_state* st, int n) {
+  const double sm = st->sigma_max;
+  return sm > 0.0 && sm <= 1024.0 && n * std::log2(1.0 + sm) < 60.0;
+}
+// A tree over a conditioned Sigma' (sampler): Sigma' >= I/2 bounds the pivot
+// determinants below by 1/4, so s <= 2^n and the sums <= 3^n; entries and
+// determinants are bounded by sigma_max and sigma_max^2.
+bool fx_ok_sigma(const gbs_state* st, int n) {
+  const double sm = st->sigma_max;
+  return sm > 0.0 && sm < 64.0 && n <= 36;
 }
 
 // ------------------------------------------------------- click blocks ---
@@ -158,6 +175,7 @@ static double unit_roundoff_b(int prec) {
     case GBS_PREC_DD: return ldexp(1.0, -102);
     case GBS_PREC_TD: return ldexp(1.0, -152);
     case GBS_PREC_FP32_DIAG: return ldexp(1.0, -24);
+    case GBS_PREC_FX: return ldexp(1.0, -140);
   }
   return 1.0;
 }
@@ -174,6 +192,8 @@ static gbs_status batch_variant(gbs_ctx* ctx, int prec, bool real, int nt, const
                                   : batch_td_cplx(ctx, nt, tr, roots, outs, status, tu);
     case GBS_PREC_FP32_DIAG: return real ? batch_fp32_real(ctx, nt, tr, roots, outs, status, tu)
                                          : batch_fp32_cplx(ctx, nt, tr, roots, outs, status, tu);
+    case GBS_PREC_FX: return real ? batch_fx_real(ctx, nt, tr, roots, outs, status, tu)
+                                  : set_error(ctx, GBS_EINVAL, "the fixed-point precision needs the real basis");
   }
   return set_error(ctx, GBS_EINVAL, "unknown precision");
 }
@@ -260,7 +280,7 @@ static void fill(gbs_prob* out, const ProbOut& r, int prec, bool real, double lo
   out->logdet_sigma = logdet;
   out->prec_used = prec;
   out->basis_used = real ? GBS_BASIS_REAL : GBS_BASIS_COMPLEX;
-  out->status = r.status == kStatusNotPD ? GBS_ENOTPD : GBS_OK;
+  out->status = r.status == kStatusNotPD ? GBS_ENOTPD : r.status == kStatusRange ? GBS_EPRECISION : GBS_OK;
 }
 
 // Probabilities of a batch of requests with the precision ladder; out[] per request.
@@ -288,31 +308,48 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
       todo.push_back(i);
     }
   }
-  const int ladder[3] = {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD};
+  // AUTO: FP64, then fixed point where the state bounds the tree (real basis),
+  // then triple-double; a request moves on while its error estimate misses
+  // rel_tol or its fixed-point tree left the range.
+  const int ladder[3] = {GBS_PREC_FP64, GBS_PREC_FX, GBS_PREC_TD};
   const int steps = prec == GBS_PREC_AUTO ? 3 : 1;
   bool uncertified = false;
   for (int k = 0; k < steps && !todo.empty(); ++k) {
     const int pr = prec == GBS_PREC_AUTO ? ladder[k] : prec;
-    std::vector<BatchTree> sub(todo.size());
-    std::vector<double> ld(todo.size());
-    for (size_t i = 0; i < todo.size(); ++i) {
-      sub[i] = trees[todo[i]];
-      ld[i] = states[todo[i]]->logdet_sigma;
+    std::vector<int> run, next;
+    for (int i : todo) {
+      if (pr == GBS_PREC_FX && !(real && fx_ok_inverse(states[i], N[i]))) {
+        if (prec == GBS_PREC_AUTO) {
+          next.push_back(i);
+          continue;
+        }
+        return set_error(ctx, GBS_EPRECISION, "the state does not bound the fixed-point tree (or basis not real)");
+      }
+      run.push_back(i);
     }
-    std::vector<ProbOut> res(todo.size());
-    if ((st = batch_eval(ctx, pr, real, (int)todo.size(), sub.data(), ctx->hbuf.ptr, ld.data(), res.data())))
+    std::vector<BatchTree> sub(run.size());
+    std::vector<double> ld(run.size());
+    for (size_t i = 0; i < run.size(); ++i) {
+      sub[i] = trees[run[i]];
+      ld[i] = states[run[i]]->logdet_sigma;
+    }
+    std::vector<ProbOut> res(run.size());
+    if ((st = batch_eval(ctx, pr, real, (int)run.size(), sub.data(), ctx->hbuf.ptr, ld.data(), res.data())))
       return st;
-    std::vector<int> next;
-    for (size_t i = 0; i < todo.size(); ++i) {
-      fill(&out[todo[i]], res[i], pr, real, ld[i]);
-      if (prec == GBS_PREC_AUTO && res[i].status == 0 && !(res[i].err <= tol * fabs(res[i].p_hi)))
-        next.push_back(todo[i]);
+    for (size_t i = 0; i < run.size(); ++i) {
+      fill(&out[run[i]], res[i], pr, real, ld[i]);
+      if (prec != GBS_PREC_AUTO) continue;
+      if (res[i].status == kStatusRange || (res[i].status == 0 && !(res[i].err <= tol * fabs(res[i].p_hi))))
+        next.push_back(run[i]);
     }
+    std::sort(next.begin(), next.end());
     todo.swap(next);
     if (k == steps - 1 && !todo.empty()) uncertified = true;
   }
-  for (int i = 0; i < nreq; ++i)
-    if (out[i].status) return set_error(ctx, out[i].status, "a pivot block is not positive definite");
+  for (int i = 0; i < nreq; ++i) {
+    if (out[i].status == GBS_ENOTPD) return set_error(ctx, GBS_ENOTPD, "a pivot block is not positive definite");
+    if (out[i].status) return set_error(ctx, out[i].status, "a fixed-point tree left its range");
+  }
   if (uncertified) return set_error(ctx, GBS_EPRECISION, "the triple-double error estimate exceeds rel_tol");
   return GBS_OK;
 }
@@ -322,7 +359,8 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
 using namespace gbs;
 
 extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, char* report, size_t report_len) {
-  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP32_DIAG || n < 6 || n > 28) return GBS_EINVAL;
+  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FX || n < 6 || n > 28) return GBS_EINVAL;
+  if (prec == GBS_PREC_FX && basis == GBS_BASIS_COMPLEX) return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
   cudaSetDevice(ctx->device);
   const bool real = basis != GBS_BASIS_COMPLEX;
@@ -400,7 +438,7 @@ done:
 
 extern "C" gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub_e, int* d_top, int* grid_per_sm,
                                      long long* level_threads) {
-  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP32_DIAG) return GBS_EINVAL;
+  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FX) return GBS_EINVAL;
   const BatchTune& t = ctx->tune[prec][basis != GBS_BASIS_COMPLEX ? 1 : 0];
   if (sub_e) *sub_e = t.sub_e;
   if (d_top) *d_top = t.d_top;
@@ -411,7 +449,7 @@ extern "C" gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub
 
 extern "C" gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_top, int grid_per_sm,
                                      long long level_threads) {
-  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP32_DIAG || sub_e < 0 || sub_e > 7 ||
+  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FX || sub_e < 0 || sub_e > 7 ||
       (sub_e > 0 && sub_e < 5) || d_top < 0 ||
       d_top > 16 || grid_per_sm < 0 || level_threads < 1)
     return GBS_EINVAL;
@@ -428,7 +466,7 @@ extern "C" gbs_status gbs_torontonian_batch(gbs_ctx* ctx, int n_req, const gbs_s
                                             const int* modes, const int* N_per, int prec, int basis, double rel_tol,
                                             gbs_prob* out) {
   if (!ctx || n_req < 0 || (n_req > 0 && (!states || !N_per || !out))) return GBS_EINVAL;
-  if (prec < GBS_PREC_AUTO || prec > GBS_PREC_FP32_DIAG) return GBS_EINVAL;
+  if (prec < GBS_PREC_AUTO || prec > GBS_PREC_FX) return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
   cudaSetDevice(ctx->device);
   std::vector<const int*> mp(n_req);

@@ -70,8 +70,8 @@ struct gbs_ctx {
   int sm_count = 0;
 
   // batched-engine launch parameters per (precision, basis): [prec][real]
-  gbs::BatchTune tune[5][2];
-  bool tuned[5][2] = {};
+  gbs::BatchTune tune[6][2];  // [gbs_prec][basis is real]
+  bool tuned[6][2] = {};
 
   // request loop (see gbs_server.cu)
   void* server = nullptr;
@@ -83,6 +83,7 @@ struct gbs_state {
   bool has_factors = false;  // built from (U, r, eta): closed-form Sigma^-1 blocks available
   double eta = 1.0;
   double logdet_sigma = 0.0;
+  double sigma_max = 0.0;  // upper bound on the largest eigenvalue of Sigma (0 = unknown)
   gbs::DevBuf U;      // M x M complex (interleaved), row-major
   gbs::DevBuf r;      // M doubles
   gbs::DevBuf alpha;  // M doubles: (1/d+ + 1/d-)/2
@@ -124,6 +125,7 @@ gbs_status batch_dd_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*,
 gbs_status batch_dd_cplx(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 gbs_status batch_td_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 gbs_status batch_td_cplx(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
+gbs_status batch_fx_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 gbs_status batch_fp32_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 gbs_status batch_fp32_cplx(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 
@@ -163,6 +165,10 @@ gbs_status traj_start(gbs_ctx* ctx, Trajectory& tj);
 gbs_status ensure_sigma_real(gbs_ctx* ctx, gbs_state* st);
 gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, int prec, gbs_sample_stats& stt);
 double unit_of(int prec);
+// Fixed-point eligibility (gbs_batch_api.cu): a tree over n modes of
+// (Sigma^-1)_S, resp. of a conditioned Sigma', keeps every value in range.
+bool fx_ok_inverse(const gbs_state* st, int n);
+bool fx_ok_sigma(const gbs_state* st, int n);
 
 // Up to 32 click modes passed by value as a kernel argument.
 struct ModeList {

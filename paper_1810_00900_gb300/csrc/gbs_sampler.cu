@@ -249,8 +249,18 @@ gbs_status ensure_sigma_real(gbs_ctx* ctx, gbs_state* st) {
 }
 
 double unit_of(int prec) {
-  return prec == GBS_PREC_FP64 ? 0x1p-53 : prec == GBS_PREC_DD ? 0x1p-102 : 0x1p-152;
+  switch (prec) {
+    case GBS_PREC_FP64: return 0x1p-53;
+    case GBS_PREC_DD: return 0x1p-102;
+    case GBS_PREC_FX: return 0x1p-140;
+  }
+  return 0x1p-152;
 }
+
+namespace {
+// Slot of a precision in gbs_sample_stats.trees / tree_seconds.
+int stat_slot(int prec) { return prec == GBS_PREC_FX ? 3 : prec - 1; }
+}  // namespace
 
 
 size_t traj_bytes(int M) {
@@ -311,11 +321,18 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
   // Bound on |delta p0|: half the near-tie threshold, so that a decision can
   // differ from an exact evaluation only for draws already counted as near ties.
   const double TOL = 5e-10;
-  auto pick = [&](double kp, int n) {
+  // AUTO ladder: FP64, fixed point (when the state bounds the tree), triple-double.
+  auto pick = [&](const Trajectory* t, double kp, int n) {
     if (prec != GBS_PREC_AUTO) return prec;
-    const int ladder[3] = {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD};
-    for (int l = 0; l < 3; ++l)
+    const int ladder[3] = {GBS_PREC_FP64, GBS_PREC_FX, GBS_PREC_TD};
+    for (int l = 0; l < 3; ++l) {
+      if (ladder[l] == GBS_PREC_FX && !fx_ok_sigma(t->st, n)) continue;
       if (4.0 * std::max(n, 1) * unit_of(ladder[l]) * kp * 2.0 < 0.5 * TOL) return ladder[l];
+    }
+    return (int)GBS_PREC_TD;
+  };
+  auto wider = [&](const Trajectory* t, int p, int n) {
+    if (p == GBS_PREC_FP64 && fx_ok_sigma(t->st, n)) return (int)GBS_PREC_FX;
     return (int)GBS_PREC_TD;
   };
   if ((e = stage_begin(ctx, act.size() * (2 * sizeof(GatherItem) + sizeof(DecideItem) + sizeof(CondItem) + 4 * 16384) +
@@ -329,7 +346,9 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
     q.tj = t;
     q.half = t->need_full ? 0 : 1;
     q.n = q.half ? t->m : t->m + 1;
-    q.prec = pick(t->kappa_prev * (q.half ? 1.5 : 8.0), q.n);
+    q.prec = pick(t, t->kappa_prev * (q.half ? 1.5 : 8.0), q.n);
+    if (q.prec == GBS_PREC_FX && !fx_ok_sigma(t->st, q.n))
+      return set_error(ctx, GBS_EPRECISION, "sampler: the state does not bound the fixed-point tree");
     todo[i] = i;
   }
   for (int round = 0; round < 4 && !todo.empty(); ++round) {
@@ -348,7 +367,7 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
     if ((e = stage(ctx, gi.data(), gi.size() * sizeof(GatherItem), &dgi))) return e;
     gather_kernel<<<(unsigned)gi.size(), 128, 0, ctx->stream>>>((const GatherItem*)dgi, (double*)ctx->hbuf.ptr);
     count_launch(ctx);
-    for (int pv : {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_TD}) {
+    for (int pv : {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_FX, GBS_PREC_TD}) {
       std::vector<size_t> grp;
       for (size_t i : todo)
         if (trees[i].prec == pv && trees[i].n > 0) grp.push_back(i);
@@ -360,8 +379,8 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
       const auto tb = std::chrono::steady_clock::now();
       if ((e = batch_eval(ctx, pv, true, (int)grp.size(), sub.data(), ctx->hbuf.ptr, zero.data(), r.data())))
         return e;
-      stt.tree_seconds[pv - 1] += std::chrono::duration<double>(std::chrono::steady_clock::now() - tb).count();
-      stt.trees[pv - 1] += (long long)grp.size();
+      stt.tree_seconds[stat_slot(pv)] += std::chrono::duration<double>(std::chrono::steady_clock::now() - tb).count();
+      stt.trees[stat_slot(pv)] += (long long)grp.size();
       stt.steps += (long long)grp.size();
       for (size_t j = 0; j < grp.size(); ++j) trees[grp[j]].res = r[j];
     }
@@ -373,6 +392,16 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
         q.res.tor[0] = 1.0;
         q.res.abs_sum = 1.0;
       }
+      if (q.res.status == kStatusRange && prec == GBS_PREC_AUTO) {  // fixed point out of range: redo in TD
+        q.half = 0;
+        q.n = q.tj->m + 1;
+        q.prec = GBS_PREC_TD;
+        next.push_back(i);
+        stt.escalations++;
+        continue;
+      }
+      if (q.res.status == kStatusRange)
+        return set_error(ctx, GBS_EPRECISION, "sampler: a fixed-point tree left its range");
       if (q.res.status) return set_error(ctx, GBS_ENOTPD, "sampler: a pivot block is not positive definite");
       const double u = unit_of(q.prec), n = std::max(q.n, 1);
       double dp;
@@ -388,7 +417,7 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
       if (prec == GBS_PREC_AUTO && !(dp < TOL) && !(q.prec == GBS_PREC_TD && !q.half)) {
         q.half = 0;
         q.n = q.tj->m + 1;
-        q.prec = std::min<int>(GBS_PREC_TD, std::max(q.prec + 1, (int)GBS_PREC_DD));
+        q.prec = wider(q.tj, q.prec, q.n);
         next.push_back(i);
         stt.escalations++;
       }
@@ -497,7 +526,8 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
                                  double* p0_out, gbs_sample_stats* stats) {
   if (!ctx || !cst || !patterns || n_samples < 1) return GBS_EINVAL;
   if (N_post < 0 || N_post > kMaxClicks || (forced_clicks && N_post < 1)) return GBS_EINVAL;
-  if (prec != GBS_PREC_AUTO && prec != GBS_PREC_FP64 && prec != GBS_PREC_DD && prec != GBS_PREC_TD)
+  if (prec != GBS_PREC_AUTO && prec != GBS_PREC_FP64 && prec != GBS_PREC_DD && prec != GBS_PREC_TD &&
+      prec != GBS_PREC_FX)
     return GBS_EINVAL;
   if (max_attempts < 1) max_attempts = 1;
   std::lock_guard<std::mutex> g(ctx->mu);

@@ -16,6 +16,7 @@
 //  - States given only by V: Sigma is inverted by Gauss-Jordan elimination
 //    (no pivoting; Sigma is Hermitian positive definite), one launch per pivot,
 //    ping-pong buffers; log det Sigma is the sum of the logs of the pivots.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -260,6 +261,9 @@ gbs_status state_build(gbs_ctx* ctx, int M, const double* U, const double* r, do
   alloc_state(ctx, M, &st);
   st->has_factors = true;
   st->eta = eta;
+  // largest eigenvalue of Sigma: max over modes of d+ = (eta e^(2|r|) + 2 - eta) / 2
+  for (int l = 0; l < M; ++l)
+    st->sigma_max = std::max(st->sigma_max, 0.5 * (eta * std::exp(2.0 * std::fabs(r[l])) + 2.0 - eta));
   const size_t MM = (size_t)M * M;
   DevBuf tmp;
   gbs_status e;
@@ -305,6 +309,12 @@ gbs_status state_from_V(gbs_ctx* ctx, int M, const double* V, gbs_state** out) {
     if (!std::isfinite(V[i])) return set_error(ctx, GBS_EINVAL, "gbs_state_from_V: non-finite V");
   gbs_state* st = nullptr;
   alloc_state(ctx, M, &st);
+  // Gershgorin bound on the largest eigenvalue of Sigma = V + I/2
+  for (long long i = 0; i < D; ++i) {
+    double row = 0.5;
+    for (long long j = 0; j < D; ++j) row += std::hypot(V[2 * (i * D + j)], V[2 * (i * D + j) + 1]);
+    st->sigma_max = std::max(st->sigma_max, row);
+  }
   DevBuf X2, piv;
   gbs_status e;
   auto fail = [&](gbs_status code) {

@@ -136,7 +136,15 @@ struct TreeOut {
 };
 
 // ------------------------------------------------- device status codes ---
-enum : int { kStatusOk = 0, kStatusNotPD = 3 };
+// kStatusRange: a fixed-point tree met a value outside the range it can carry
+// (the caller redoes the tree in floating point).
+enum : int { kStatusOk = 0, kStatusNotPD = 3, kStatusRange = 5 };
+template <class T> constexpr int bad_status() { return kStatusNotPD; }
+
+GBS_HD bool is_pos(double x) { return x > 0.0; }
+GBS_HD bool is_pos(float x) { return x > 0.0f; }
+GBS_HD bool is_pos(const dd& x) { return x.hi > 0.0; }
+GBS_HD bool is_pos(const td& x) { return x.x0 > 0.0; }
 
 // --------------------------------------------------- breadth-first level --
 // Parents: count nodes with q undecided modes, entry e of node i at par[e*count + i].

@@ -54,12 +54,27 @@ def test_n24_triple_double_matches_oracle(ctx_state):
     assert abs(pr.abs_sum - abs_ref) <= 1e-12 * abs_ref
 
 
+def test_n24_fixed_point_matches_oracle(ctx_state):
+    ctx, st, modes = ctx_state
+    tor_ref, abs_ref, p_ref = golden()
+    pr = gbs.torontonian(ctx, st, modes, "fx", "real")
+    assert abs(pr.tor_value - tor_ref) <= 1e-9 * abs(tor_ref)
+    assert abs(pr.p - p_ref) <= 1e-9 * abs(p_ref)
+    assert abs(pr.abs_sum - abs_ref) <= 1e-12 * abs_ref
+    assert pr.err_bound <= 1e-12 * abs(pr.p)
+
+
 def test_n24_auto_reaches_tolerance(ctx_state):
     ctx, st, modes = ctx_state
     tor_ref, _, p_ref = golden()
     pr = gbs.torontonian(ctx, st, modes, "auto", "real")
-    assert pr.prec == "td"  # kappa ~ 1e26: FP64 and double-double cannot certify 1e-9
+    # kappa ~ 1e26: FP64 cannot certify 1e-9; the state bounds the tree, so the
+    # fixed-point rung (before triple-double) is the one that does
+    assert pr.prec == "fx"
     assert abs(pr.p - p_ref) <= 1e-9 * abs(p_ref)
+    pc = gbs.torontonian(ctx, st, modes, "auto", "complex")
+    assert pc.prec == "td"  # fixed point is real-basis only
+    assert abs(pc.p - p_ref) <= 1e-9 * abs(p_ref)
 
 
 def test_n24_fp64_throughput_configuration_sums_all_terms(ctx_state):

@@ -43,7 +43,7 @@ def test_forced_trajectories_p0_every_step(ctx):
         assert np.allclose(p0[i], np.array(ref["p0"]), rtol=0, atol=1e-10), (p0[i], ref["p0"])
 
 
-@pytest.mark.parametrize("prec", ["auto", "dd"])
+@pytest.mark.parametrize("prec", ["auto", "dd", "fx"])
 def test_free_samples_match_oracle(ctx, prec):
     M = 6
     st, Sig = make(ctx, M, 21, r=(0.6, 1.1), eta=0.9)
@@ -91,3 +91,16 @@ def test_bigger_forced_trajectory_sampled_steps(ctx):
     # one tree per step once the first click is in (steps before it need none)
     assert 0 < stats["steps"] <= 2 * M
     assert np.all(np.isfinite(p0[0])) and np.all((p0[0] > 0) & (p0[0] < 1))
+
+
+def test_forced_trajectory_fixed_point_equals_triple_double(ctx):
+    # 40 modes, 12 forced clicks: p0 at every step in fixed point and in
+    # triple-double agree far below the 5e-10 target
+    M = 40
+    st, Sig = make(ctx, M, 8, r=(0.4, 0.9), eta=0.9)
+    forced = gi.random_modes(M, 12, 8, stream="clicks")[None, :].astype(np.int32)
+    _, p_fx, s_fx, st1 = gbs.sample(ctx, st, 1, seed=3, N_post=12, forced_clicks=forced, prec="fx", want_p0=True)
+    _, p_td, s_td, st2 = gbs.sample(ctx, st, 1, seed=3, N_post=12, forced_clicks=forced, prec="td", want_p0=True)
+    assert st1 == 0 and st2 == 0
+    assert np.max(np.abs(p_fx - p_td)) < 1e-20
+    assert s_fx["trees"][3] > 0 and s_fx["trees"][2] == 0 and s_td["trees"][2] > 0
