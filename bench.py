@@ -162,6 +162,7 @@ def sampler_block(ctx, gbs, gi, n_traj, ws, local):
     stp, clicks = gi.chain_sampling_workload(800, 20, n_traj, seed=2)
     st = gbs.build_state(ctx, stp.U, stp.r, stp.eta)
     ctx.autotune("fx", "real", 18)
+    ctx.autotune("fxw", "real", 18)
     ctx.autotune("td", "real", 18)
     forced = np.array(clicks, dtype=np.int32)
     gbs.sample(ctx, st, 2, seed=2, N_post=20, forced_clicks=forced[:2])  # warm-up
@@ -175,12 +176,30 @@ def sampler_block(ctx, gbs, gi, n_traj, ws, local):
             "seconds": dt, "trajectories": n_traj, "steps_evaluated": stats["steps"],
             "escalations": stats["escalations"], "uncertified_steps": stats["uncertified"],
             "gpu_launches": ctx.launch_count - l0,
-            "trees_fp64_dd_td_fx": stats["trees"], "tree_seconds_fp64_dd_td_fx": stats["tree_seconds"],
-            "other_seconds": stats["cond_seconds"], "fx_tuning": ctx.tuning("fx", "real"),
+            "trees_fp64_dd_td_fx_fxw": stats["trees"], "tree_seconds_fp64_dd_td_fx_fxw": stats["tree_seconds"],
+            "other_seconds": stats["cond_seconds"], "fx_tuning": ctx.tuning("fx", "real"), "fxw_tuning": ctx.tuning("fxw", "real"),
             "td_tuning": ctx.tuning("td", "real"),
             "p0_range": [float(p0.min()), float(p0.max())], "status": status,
             "workload": "M=800 modes, r~U[0.3,0.9], Haar seed 2, eta=1; %d forced trajectories with 20 uniform "
                         "click positions; no-click probability at every one of the 800 steps" % n_traj}
+
+
+def certified_block(ctx, gbs, st, modes, steps, stream):
+    """The same N = 24 Torontonian evaluated to the 1e-10 relative tolerance (AUTO precision),
+    device time per evaluation, next to the FP64 throughput figure of the headline."""
+    gbs.torontonian(ctx, st, modes, "auto", "real")
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    res = []
+    for i in range(steps):
+        ev[i][0].record(stream)
+        res.append(gbs.torontonian(ctx, st, modes, "auto", "real"))
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    return {"metric": "certified Tor subset-terms/s (N=24, rel. error bound <= 1e-10)",
+            "value": 2.0 ** 24 / (ms * 1e-3), "ms_per_evaluation": ms, "prec": res[-1].prec,
+            "rel_err_bound": res[-1].err_bound / abs(res[-1].p), "kappa": res[-1].kappa, "p": res[-1].p}
 
 
 def walltime_block(ctx, gbs, gi, ms):
@@ -198,7 +217,7 @@ def walltime_block(ctx, gbs, gi, ms):
         dt = time.perf_counter() - t0
         st.free()
         rows.append({"m": m, "modes": int(stp.U.shape[0]), "seconds_per_sample": dt, "status": status,
-                     "trees_fp64_dd_td_fx": stats["trees"], "tree_seconds_fp64_dd_td_fx": stats["tree_seconds"],
+                     "trees_fp64_dd_td_fx_fxw": stats["trees"], "tree_seconds_fp64_dd_td_fx_fxw": stats["tree_seconds"],
                      "escalations": stats["escalations"], "uncertified_steps": stats["uncertified"],
                      "p0_min": float(p0.min()),
                      "paper_titan_hours": paper[m][0], "paper_titan_nodes": paper[m][1]})
@@ -344,7 +363,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "dd", "td", "fp32"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "dd", "td", "fp32", "fx", "fxw"])
     ap.add_argument("--basis", default="real", choices=["real", "complex"])
     ap.add_argument("--N", type=int, default=24)
     ap.add_argument("--cpu-sample", type=int, default=19, help="click count of the oracle's CPU sample")
@@ -395,7 +414,8 @@ def main():
         tune_report = ctx.autotune(args.prec, args.basis, min(args.N, 22)) if not args.no_autotune else []
     tuning = ctx.tuning(args.prec, args.basis)
     Q = {("fp64", False): 5, ("fp64", True): 4, ("dd", False): 4, ("dd", True): 3, ("td", False): 3,
-         ("td", True): 2, ("fp32", False): 5, ("fp32", True): 4}[(args.prec, complex_basis)]
+         ("td", True): 2, ("fp32", False): 5, ("fp32", True): 4, ("fx", False): 3,
+         ("fxw", False): 3}[(args.prec, complex_basis)]
     Q = min(Q, args.N)
     q_root = min(args.N, Q + tuning["sub_e"])
     depth = args.N - q_root
@@ -470,7 +490,8 @@ def main():
             "workload": "single Torontonian, N=%d clicks of the M=200 pure state (r=0.8, Haar seed 1): "
                         "2^%d subset determinants per step" % (args.N, args.N),
             "M": 200, "N": args.N, "basis": args.basis, "per_term_arithmetic": args.prec,
-            "sum": "double-double" if args.prec in ("fp64", "dd", "fp32") else "triple-double",
+            "sum": {"fp64": "double-double", "dd": "double-double", "fp32": "double-double", "td": "triple-double",
+                    "fx": "exact fixed point", "fxw": "exact fixed point"}[args.prec],
             "l2": "flushed between steps (256 MB write); tree level buffers also exceed L2",
             "parallelism": "replicas" if ws > 1 else "single GPU",
             "tuning": tuning, "autotune_candidates": len(tune_report),
@@ -488,6 +509,8 @@ def main():
         "clocks": clk,
         "result": {"p": results[-1].p, "kappa": results[-1].kappa, "prec": results[-1].prec},
     }
+    if args.prec == "fp64" and args.N == 24:
+        line["certified"] = certified_block(ctx, gbs, st, modes, max(3, args.steps // 2), stream)
     if args.sampler_traj > 0:
         line["sampler"] = sampler_block(ctx, gbs, gi, args.sampler_traj, ws, local)
     if args.batched_req > 0:

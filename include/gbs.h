@@ -59,15 +59,17 @@ typedef int gbs_status;
 
 /* Per-term arithmetic of the subset enumeration. */
 typedef enum {
-  GBS_PREC_AUTO = 0,       /* cheapest of FP64 / FX / TD whose error estimate meets rel_tol */
+  GBS_PREC_AUTO = 0,       /* cheapest of FP64 / FX / FXW / TD whose error estimate meets rel_tol */
   GBS_PREC_FP64 = 1,       /* IEEE double */
   GBS_PREC_DD = 2,         /* double-double, ~106-bit significand */
   GBS_PREC_TD = 3,         /* triple-double, ~159-bit significand */
   GBS_PREC_FP32_DIAG = 4,  /* FP32 terms, FP64 sums: diagnostic only */
-  GBS_PREC_FX = 5          /* fixed point, 224-bit integers on the integer pipe:
+  GBS_PREC_FX = 5,         /* fixed point, 224-bit integers on the integer pipe:
                               160 fraction bits, range +-2^63; real basis only, and
                               only where the state bounds every value of the tree
                               (otherwise GBS_EPRECISION, or TD under AUTO) */
+  GBS_PREC_FXW = 6         /* wide fixed point, 256-bit integers: 192 fraction bits,
+                              same range and conditions as GBS_PREC_FX */
 } gbs_prec;
 
 /* Basis of the matrices the enumeration factors.  Both give identical
@@ -187,8 +189,8 @@ typedef struct {
   long long near_ties;    /* coin draws with |u - p0| < 1e-9 */
   long long rejections;   /* trajectories abandoned by postselection (each may retry) */
   double seconds;         /* wall time of the call */
-  long long trees[4];     /* subset trees evaluated in FP64, DD, TD, FX */
-  double tree_seconds[4]; /* wall time spent in those tree batches */
+  long long trees[5];     /* subset trees evaluated in FP64, DD, TD, FX, FXW */
+  double tree_seconds[5]; /* wall time spent in those tree batches */
   double cond_seconds;    /* wall time of gathers, decisions and conditioning */
   long long uncertified;  /* steps whose p0 error bound stayed above 5e-10 even in TD */
 } gbs_sample_stats;
@@ -211,8 +213,8 @@ typedef struct {
  *                  preset (click iff the mode is listed) while p0 is still
  *                  evaluated at every step;
  *   prec           GBS_PREC_AUTO (per trajectory and step, the cheapest of FP64 /
- *                  FX / TD keeping the estimated error of p0 below 5e-10, half the
- *                  near-tie threshold) or a fixed GBS_PREC_FP64 / DD / TD / FX;
+ *                  FX / FXW / TD keeping the estimated error of p0 below 5e-10,
+ *                  half the near-tie threshold) or a fixed FP64 / DD / TD / FX / FXW;
  *   patterns       caller-owned n_samples x M bytes (1 = click);
  *   p0_out         NULL or caller-owned n_samples x M doubles, p0 of step s of
  *                  sample i at [i * M + s] (last attempt);
@@ -236,7 +238,7 @@ typedef struct {
   uint64_t seed;           /* SAMPLE: coin stream seed (as gbs_sample) */
   int sample_index;        /* SAMPLE: sample index of the coin counter, 0 <= index < 2^20 */
   int max_attempts;        /* SAMPLE: postselection attempts (>= 1) */
-  int prec;                /* gbs_prec (SAMPLE: AUTO, FP64, DD, TD or FX) */
+  int prec;                /* gbs_prec (SAMPLE: AUTO, FP64, DD, TD, FX or FXW) */
   int basis;               /* PROB: gbs_basis */
   double rel_tol;          /* PROB: as gbs_torontonian */
 } gbs_request;
@@ -312,7 +314,7 @@ gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_to
  * interleaved (basis GBS_BASIS_COMPLEX) or real (GBS_BASIS_REAL), Hermitian /
  * symmetric positive definite (only the lower triangle is read).
  * inc, exc, tor: caller-owned double[3] each (may be NULL), unevaluated sums.
- * prec must not be GBS_PREC_AUTO; GBS_PREC_FX needs the real basis and a matrix
+ * prec must not be GBS_PREC_AUTO; GBS_PREC_FX / FXW need the real basis and a matrix
  * whose eigenvalues lie in [2^-10, 2^10] with (1 + 1/lambda_min)^n < 2^60
  * (checked on the host; otherwise GBS_EPRECISION).
  * Errors: GBS_EINVAL, GBS_ENOTPD, GBS_EPRECISION, GBS_ECUDA. */

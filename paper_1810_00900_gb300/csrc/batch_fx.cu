@@ -1,4 +1,4 @@
-// Batched subset-determinant trees, fixed-point per-term arithmetic (real basis).
+// Batched subset-determinant trees, fixed-point (160 fraction bits) per-term arithmetic (real basis).
 #include "gbs_fx.cuh"
 #include "gbs_batch_driver.cuh"
 

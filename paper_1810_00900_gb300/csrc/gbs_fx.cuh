@@ -4,12 +4,13 @@
 // ~1e20.  Built from FP64 error-free transformations (triple-double) each
 // operation costs ~30 FP64 instructions, and this GPU issues only 2 FP64 FMAs
 // per clock per SM, against ~60 32-bit integer multiply-adds and carry-chained
-// adds.  fx holds a two's-complement integer X of kFxL 32-bit limbs (limb 0
-// least significant) read as X * 2^(-32 kFxF): 160 fraction bits and a range
-// of +-2^63.  Additions are exact (one carry-chained instruction per limb);
-// a product keeps the columns at and above the fraction point of the exact
-// 448-bit product (partial products a_i b_j with i + j >= kFxF - 2), which
-// leaves an error of at most two units of 2^-160, biased low.
+// adds.  fxn<L> holds a two's-complement integer X of L 32-bit limbs (limb 0
+// least significant) read as X * 2^(-32 (L-2)): fx = fxn<7> has 160 fraction
+// bits, fxw = fxn<8> 192, both a range of +-2^63.  Additions are exact (one
+// carry-chained instruction per limb); a product keeps the columns at and
+// above the fraction point of the exact 2L-limb product (partial products
+// a_i b_j with i + j >= L - 4), which leaves an error of at most two units of
+// the last place, biased low.
 //
 // Inside the tree every value stays in range when the caller has checked it:
 // entries are bounded by the largest eigenvalue of the root, pivot
@@ -27,12 +28,13 @@
 
 namespace gbs {
 
-constexpr int kFxL = 7;  // limbs
-constexpr int kFxF = 5;  // fraction limbs
-
-struct fx {
-  uint32_t w[kFxL];
+// fxn<L>: L limbs, L - 2 of them fraction limbs (range +-2^63 in every width).
+template <int L>
+struct fxn {
+  uint32_t w[L];
 };
+typedef fxn<7> fx;   // 160 fraction bits (GBS_PREC_FX)
+typedef fxn<8> fxw;  // 192 fraction bits (GBS_PREC_FXW)
 
 // ------------------------------------------------ carry-chained primitives --
 // The carry flag lives between consecutive volatile asm statements of one
@@ -58,48 +60,53 @@ GBS_HD uint32_t madc_hi_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; GBS
 #undef GBS_ASM2
 
 // ---------------------------------------------------------------- basics --
-GBS_HD fx operator+(const fx& a, const fx& b) {
-  fx r;
+template <int L>
+GBS_HD fxn<L> operator+(const fxn<L>& a, const fxn<L>& b) {
+  fxn<L> r;
   r.w[0] = add_cc(a.w[0], b.w[0]);
 #pragma unroll
-  for (int k = 1; k < kFxL - 1; ++k) r.w[k] = addc_cc(a.w[k], b.w[k]);
-  r.w[kFxL - 1] = addc(a.w[kFxL - 1], b.w[kFxL - 1]);
+  for (int k = 1; k < L - 1; ++k) r.w[k] = addc_cc(a.w[k], b.w[k]);
+  r.w[L - 1] = addc(a.w[L - 1], b.w[L - 1]);
   return r;
 }
-GBS_HD fx operator-(const fx& a, const fx& b) {
-  fx r;
+template <int L>
+GBS_HD fxn<L> operator-(const fxn<L>& a, const fxn<L>& b) {
+  fxn<L> r;
   r.w[0] = sub_cc(a.w[0], b.w[0]);
 #pragma unroll
-  for (int k = 1; k < kFxL - 1; ++k) r.w[k] = subc_cc(a.w[k], b.w[k]);
-  r.w[kFxL - 1] = subc(a.w[kFxL - 1], b.w[kFxL - 1]);
+  for (int k = 1; k < L - 1; ++k) r.w[k] = subc_cc(a.w[k], b.w[k]);
+  r.w[L - 1] = subc(a.w[L - 1], b.w[L - 1]);
   return r;
 }
-GBS_HD fx operator-(const fx& a) {
-  fx r;
+template <int L>
+GBS_HD fxn<L> operator-(const fxn<L>& a) {
+  fxn<L> r;
   r.w[0] = sub_cc(0u, a.w[0]);
 #pragma unroll
-  for (int k = 1; k < kFxL - 1; ++k) r.w[k] = subc_cc(0u, a.w[k]);
-  r.w[kFxL - 1] = subc(0u, a.w[kFxL - 1]);
+  for (int k = 1; k < L - 1; ++k) r.w[k] = subc_cc(0u, a.w[k]);
+  r.w[L - 1] = subc(0u, a.w[L - 1]);
   return r;
 }
 // x / 2 (arithmetic shift by one bit)
-GBS_HD fx fx_half(const fx& a) {
-  fx r;
+template <int L>
+GBS_HD fxn<L> fx_half(const fxn<L>& a) {
+  fxn<L> r;
 #pragma unroll
-  for (int k = 0; k < kFxL - 1; ++k) r.w[k] = (a.w[k] >> 1) | (a.w[k + 1] << 31);
-  r.w[kFxL - 1] = (uint32_t)((int32_t)a.w[kFxL - 1] >> 1);
+  for (int k = 0; k < L - 1; ++k) r.w[k] = (a.w[k] >> 1) | (a.w[k + 1] << 31);
+  r.w[L - 1] = (uint32_t)((int32_t)a.w[L - 1] >> 1);
   return r;
 }
 
 // ---------------------------------------------------------------- product --
-// Window of the unsigned product: columns kFxF - 1 (a guard column whose only
-// use is its carry) to kFxF + kFxL - 1.  Low and high halves of the partial
+// Window of the unsigned product: columns F - 1 (a guard column whose only use
+// is its carry) to F + L - 1, F = L - 2.  Low and high halves of the partial
 // products are summed in two arrays; in either array the carry out of row i
 // lands in a column that no earlier row has reached, so one add captures it.
-// The two's-complement correction subtracts b (resp. a) shifted by kFxL limbs
+// The two's-complement correction subtracts b (resp. a) shifted by L limbs
 // when a (resp. b) is negative.
-GBS_HD fx operator*(const fx& a, const fx& b) {
-  constexpr int L = kFxL, F = kFxF, W = L + 1, C0 = F - 1;  // C0: column of word 0
+template <int L>
+GBS_HD fxn<L> operator*(const fxn<L>& a, const fxn<L>& b) {
+  constexpr int F = L - 2, W = L + 1, C0 = F - 1;  // C0: column of word 0
   uint32_t lo[W], hi[W];
 #pragma unroll
   for (int k = 0; k < W; ++k) lo[k] = hi[k] = 0u;
@@ -126,7 +133,7 @@ GBS_HD fx operator*(const fx& a, const fx& b) {
       }
     }
   }
-  fx r;
+  fxn<L> r;
   (void)add_cc(lo[0], hi[0]);
 #pragma unroll
   for (int k = 0; k < L - 1; ++k) r.w[k] = addc_cc(lo[k + 1], hi[k + 1]);
@@ -146,10 +153,10 @@ GBS_HD fx operator*(const fx& a, const fx& b) {
 }
 
 // ----------------------------------------------------------- conversions --
-// Exact for |x| < 2^62 down to 2^-160 (bits below are dropped, toward zero).
-template <>
-GBS_HD fx from_double<fx>(double x) {
-  fx r;
+// Exact for |x| < 2^62 down to 2^-(32 (L-2)) (bits below are dropped, toward zero).
+template <int L>
+GBS_HD fxn<L> fx_from_double(double x) {
+  fxn<L> r;
 #ifdef __CUDA_ARCH__
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
 #else
@@ -158,85 +165,93 @@ GBS_HD fx from_double<fx>(double x) {
 #endif
   const int e = (int)((bits >> 52) & 0x7ff);
   const unsigned long long m = (bits & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
-  const int sh = (e ? e : 1) - 1075 + 32 * kFxF;  // bit position of m's last bit in X
+  const int sh = (e ? e : 1) - 1075 + 32 * (L - 2);  // bit position of m's last bit in X
 #pragma unroll
-  for (int k = 0; k < kFxL; ++k) {
+  for (int k = 0; k < L; ++k) {
     const int s = 32 * k - sh;
     const unsigned long long v = s >= 0 ? (s < 64 ? (m >> s) : 0ull) : (s > -64 ? (m << (-s)) : 0ull);
     r.w[k] = (uint32_t)v;
   }
   return (bits >> 63) ? -r : r;
 }
+template <> GBS_HD fx from_double<fx>(double x) { return fx_from_double<7>(x); }
+template <> GBS_HD fxw from_double<fxw>(double x) { return fx_from_double<8>(x); }
 
 // Nearest-ish double (a few units of the last place).
-GBS_HD double to_double(const fx& a) {
-  double v = (double)(int32_t)a.w[kFxL - 1];
+template <int L>
+GBS_HD double to_double(const fxn<L>& a) {
+  double v = (double)(int32_t)a.w[L - 1];
 #pragma unroll
-  for (int k = kFxL - 2; k >= 0; --k) v = fma(v, 4294967296.0, (double)a.w[k]);
-  return v * 0x1p-160;
+  for (int k = L - 2; k >= 0; --k) v = fma(v, 4294967296.0, (double)a.w[k]);
+  return v * (L == 7 ? 0x1p-160 : 0x1p-192);
 }
-static_assert(kFxF == 5, "to_double scales by 2^-(32 kFxF)");
+static_assert(sizeof(fx) == 28 && sizeof(fxw) == 32, "fx widths");
 
 // ------------------------------------------------------ tree interface ----
-GBS_HD fx fms(const fx& x, const fx& a, const fx& b) { return x - a * b; }
-GBS_HD fx fpa(const fx& x, const fx& a, const fx& b) { return x + a * b; }
-template <>
-GBS_HD fx scale_<fx, fx>(const fx& x, const fx& s) { return x * s; }
-template <>
-GBS_HD fx conv_entry<fx>(const double& x) { return from_double<fx>(x); }
+template <int L> GBS_HD fxn<L> fms(const fxn<L>& x, const fxn<L>& a, const fxn<L>& b) { return x - a * b; }
+template <int L> GBS_HD fxn<L> fpa(const fxn<L>& x, const fxn<L>& a, const fxn<L>& b) { return x + a * b; }
+template <> GBS_HD fx scale_<fx, fx>(const fx& x, const fx& s) { return x * s; }
+template <> GBS_HD fxw scale_<fxw, fxw>(const fxw& x, const fxw& s) { return x * s; }
+template <> GBS_HD fx conv_entry<fx>(const double& x) { return from_double<fx>(x); }
+template <> GBS_HD fxw conv_entry<fxw>(const double& x) { return from_double<fxw>(x); }
 
 // A pivot determinant the fixed-point tree can use: in [2^-20, 2^12), where
 // its inverse square root keeps ~150 bits (the resolution is absolute, so the
-// relative error of 1/sqrt(x) grows like 2^-160 x).
-GBS_HD bool fx_det_in_range(const fx& d) {
-  return d.w[6] == 0u && d.w[5] < (1u << 12) && (d.w[5] != 0u || d.w[4] >= (1u << 12));
+// relative error of 1/sqrt(x) grows like 2^-(32 (L-2)) x).
+template <int L>
+GBS_HD bool fx_det_in_range(const fxn<L>& d) {
+  return d.w[L - 1] == 0u && d.w[L - 2] < (1u << 12) && (d.w[L - 2] != 0u || d.w[L - 3] >= (1u << 12));
 }
-static_assert(kFxL == 7 && kFxF == 5, "limb indices of fx_det_in_range");
-GBS_HD bool not_positive(const fx& d) { return !fx_det_in_range(d); }
+template <int L> GBS_HD bool not_positive(const fxn<L>& d) { return !fx_det_in_range(d); }
+template <int L> GBS_HD bool is_pos(const fxn<L>& d) { return fx_det_in_range(d); }
 template <> constexpr int bad_status<fx>() { return kStatusRange; }
-GBS_HD bool is_pos(const fx& d) { return fx_det_in_range(d); }
+template <> constexpr int bad_status<fxw>() { return kStatusRange; }
 
-// 1/sqrt(x) for x in [2^-20, 2^12): FP64 seed from the top three limbs, then
-// two Newton steps y <- y + y (1 - x y^2) / 2 (53 -> 106 -> 160+ bits).
-__device__ __forceinline__ fx rsqrt_(const fx& x) {
-  const double xd = fma((double)x.w[4], 0x1p-32, (double)x.w[5]) + (double)x.w[3] * 0x1p-64;
-  fx y = from_double<fx>(rsqrt(xd));
-  fx one;
+// 1/sqrt(x) for x in [2^-20, 2^12): FP64 seed from the top limbs below the
+// sign limb, then Newton steps y <- y + y (1 - x y^2) / 2 (53 -> 106 -> 212 bits).
+template <int L>
+__device__ __forceinline__ fxn<L> rsqrt_(const fxn<L>& x) {
+  const double xd = fma((double)x.w[L - 3], 0x1p-32, (double)x.w[L - 2]) + (double)x.w[L - 4] * 0x1p-64;
+  fxn<L> y = fx_from_double<L>(rsqrt(xd));
+  fxn<L> one;
 #pragma unroll
-  for (int k = 0; k < kFxL; ++k) one.w[k] = k == kFxF ? 1u : 0u;
+  for (int k = 0; k < L; ++k) one.w[k] = k == L - 2 ? 1u : 0u;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
-    const fx e = one - x * (y * y);
+    const fxn<L> e = one - x * (y * y);
     y = y + fx_half(y * e);
   }
   return y;
 }
 
 // ------------------------------------------------------ sums and reduction --
-template <> struct acc_traits<fx> { typedef fx Acc; typedef fx Red; };
-GBS_HD void acc_add(fx& a, const fx& x) { a = a + x; }
-GBS_HD void acc_sub(fx& a, const fx& x) { a = a - x; }
-GBS_HD void acc_fpa(fx& acc, const fx& a, const fx& b) { acc = acc + a * b; }
-GBS_HD fx red_diff(const fx& a, const fx& b, fx*) { return a - b; }
-GBS_HD fx to_red(const fx& a, fx*) { return a; }
-GBS_HD fx red_add(const fx& a, const fx& b) { return a + b; }
-GBS_HD fx red_neg(const fx& a) { return -a; }
+template <int L> struct acc_traits<fxn<L>> { typedef fxn<L> Acc; typedef fxn<L> Red; };
+template <int L> GBS_HD void acc_add(fxn<L>& a, const fxn<L>& x) { a = a + x; }
+template <int L> GBS_HD void acc_sub(fxn<L>& a, const fxn<L>& x) { a = a - x; }
+template <int L> GBS_HD void acc_fpa(fxn<L>& acc, const fxn<L>& a, const fxn<L>& b) { acc = acc + a * b; }
+template <int L> GBS_HD fxn<L> red_diff(const fxn<L>& a, const fxn<L>& b, fxn<L>*) { return a - b; }
+template <int L> GBS_HD fxn<L> to_red(const fxn<L>& a, fxn<L>*) { return a; }
+template <int L> GBS_HD fxn<L> red_add(const fxn<L>& a, const fxn<L>& b) { return a + b; }
+template <int L> GBS_HD fxn<L> red_neg(const fxn<L>& a) { return -a; }
 template <> GBS_HD fx red_zero<fx>() { return from_double<fx>(0.0); }
+template <> GBS_HD fxw red_zero<fxw>() { return from_double<fxw>(0.0); }
 // Three doubles whose sum is the value to ~2^-159 relative (each the nearest
 // double of what the previous ones left over; the differences are exact).
-GBS_HD void red_store(const fx& a, double* o) {
+template <int L>
+GBS_HD void red_store(const fxn<L>& a, double* o) {
   const double x0 = to_double(a);
-  const fx r1 = a - from_double<fx>(x0);
+  const fxn<L> r1 = a - fx_from_double<L>(x0);
   const double x1 = to_double(r1);
-  const fx r2 = r1 - from_double<fx>(x1);
+  const fxn<L> r2 = r1 - fx_from_double<L>(x1);
   o[0] = x0;
   o[1] = x1;
   o[2] = to_double(r2);
 }
-__device__ __forceinline__ fx shfl_down(const fx& v, int off) {
-  fx r;
+template <int L>
+__device__ __forceinline__ fxn<L> shfl_down(const fxn<L>& v, int off) {
+  fxn<L> r;
 #pragma unroll
-  for (int k = 0; k < kFxL; ++k) r.w[k] = __shfl_down_sync(0xffffffffu, v.w[k], off);
+  for (int k = 0; k < L; ++k) r.w[k] = __shfl_down_sync(0xffffffffu, v.w[k], off);
   return r;
 }
 

@@ -54,10 +54,11 @@ def test_n24_triple_double_matches_oracle(ctx_state):
     assert abs(pr.abs_sum - abs_ref) <= 1e-12 * abs_ref
 
 
-def test_n24_fixed_point_matches_oracle(ctx_state):
+@pytest.mark.parametrize("prec", ["fx", "fxw"])
+def test_n24_fixed_point_matches_oracle(ctx_state, prec):
     ctx, st, modes = ctx_state
     tor_ref, abs_ref, p_ref = golden()
-    pr = gbs.torontonian(ctx, st, modes, "fx", "real")
+    pr = gbs.torontonian(ctx, st, modes, prec, "real")
     assert abs(pr.tor_value - tor_ref) <= 1e-9 * abs(tor_ref)
     assert abs(pr.p - p_ref) <= 1e-9 * abs(p_ref)
     assert abs(pr.abs_sum - abs_ref) <= 1e-12 * abs_ref

@@ -5,7 +5,8 @@ terms carries a relative error of at most about 4 n u (n rank-2 Schur steps and
 one inverse square root), so |Tor_gpu - Tor_exact| <= 8 n u sum|terms| with
 u = 2^-53 (FP64), 2^-102 (double-double), 2^-152 (triple-double); the
 fixed-point type's errors are absolute (2^-160 per operation), covered by
-u = 2^-140 for the matrices here (entries O(1), abs sum >= 1).
+u = 2^-140 for the matrices here (entries O(1), abs sum >= 1); the wide type
+(2^-192) is limited by the three-double tree output, u = 2^-158.
 """
 from fractions import Fraction
 
@@ -19,7 +20,8 @@ from helpers import frac3, real_basis_block
 
 pytestmark = pytest.mark.gpu
 
-U_OF = {"fp64": 2.0 ** -53, "dd": 2.0 ** -102, "td": 2.0 ** -152, "fp32": 2.0 ** -24, "fx": 2.0 ** -140}
+U_OF = {"fp64": 2.0 ** -53, "dd": 2.0 ** -102, "td": 2.0 ** -152, "fp32": 2.0 ** -24, "fx": 2.0 ** -140,
+        "fxw": 2.0 ** -158}
 
 
 @pytest.fixture(scope="module")
@@ -114,27 +116,30 @@ def test_not_positive_definite_is_reported(ctx):
     assert tor[0] == 0.0
 
 
+@pytest.mark.parametrize("prec", ["fx", "fxw"])
 @pytest.mark.parametrize("N", [1, 2, 3, 5, 8, 11, 13])
-def test_parity_fixed_point(ctx, N):
-    check(ctx, haar_H(N), "fx", "real")
+def test_parity_fixed_point(ctx, prec, N):
+    check(ctx, haar_H(N), prec, "real")
 
 
-def test_parity_fixed_point_n14_lossy_and_n16_relative(ctx):
-    check(ctx, haar_H(14, seed=5, M=100, r=0.6, eta=0.5), "fx", "real")
+@pytest.mark.parametrize("prec", ["fx", "fxw"])
+def test_parity_fixed_point_n14_lossy_and_n16_relative(ctx, prec):
+    check(ctx, haar_H(14, seed=5, M=100, r=0.6, eta=0.5), prec, "real")
     G = real_basis_block(haar_H(16))
     ref, _ = oracle.torontonian(G.astype(np.complex128))
-    _, _, tor, _ = gbs.subset_sum(ctx, G, "real", "fx")
+    _, _, tor, _ = gbs.subset_sum(ctx, G, "real", prec)
     rel = abs(float((frac3(tor) - ref.to_fraction()) / ref.to_fraction()))
     assert rel < 1e-20, rel
 
 
-def test_fixed_point_exact_cases(ctx):
+@pytest.mark.parametrize("prec", ["fx", "fxw"])
+def test_fixed_point_exact_cases(ctx, prec):
     # vacuum: every term is 1, the alternating sum is exactly zero
-    _, _, tor, a = gbs.subset_sum(ctx, np.eye(16), "real", "fx")
+    _, _, tor, a = gbs.subset_sum(ctx, np.eye(16), "real", prec)
     assert list(tor) == [0.0, 0.0, 0.0] and a == 2.0 ** 8
     # independent modes: Tor = prod (det(G_j)^(-1/2) - 1), here with det G_j = 1/4
     G = np.kron(np.eye(6), np.diag([0.5, 0.5]))
-    _, _, tor, _ = gbs.subset_sum(ctx, G, "real", "fx")
+    _, _, tor, _ = gbs.subset_sum(ctx, G, "real", prec)
     assert frac3(tor) == Fraction(1)
 
 
