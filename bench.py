@@ -187,6 +187,7 @@ def sampler_block(ctx, gbs, gi, n_traj, ws, local):
 def certified_block(ctx, gbs, st, modes, steps, stream):
     """The same N = 24 Torontonian evaluated to the 1e-10 relative tolerance (AUTO precision),
     device time per evaluation, next to the FP64 throughput figure of the headline."""
+    ctx.autotune("fx", "real", 22)
     gbs.torontonian(ctx, st, modes, "auto", "real")
     import torch
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -199,7 +200,8 @@ def certified_block(ctx, gbs, st, modes, steps, stream):
     ms = sum(a.elapsed_time(b) for a, b in ev) / steps
     return {"metric": "certified Tor subset-terms/s (N=24, rel. error bound <= 1e-10)",
             "value": 2.0 ** 24 / (ms * 1e-3), "ms_per_evaluation": ms, "prec": res[-1].prec,
-            "rel_err_bound": res[-1].err_bound / abs(res[-1].p), "kappa": res[-1].kappa, "p": res[-1].p}
+            "rel_err_bound": res[-1].err_bound / abs(res[-1].p), "kappa": res[-1].kappa, "p": res[-1].p,
+            "fx_tuning": ctx.tuning("fx", "real")}
 
 
 def walltime_block(ctx, gbs, gi, ms):
@@ -370,7 +372,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=16, help="click count per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--tuning", default="", help="sub_e,d_top,grid_per_sm,level_threads (skips the autotuner)")
+    ap.add_argument("--tuning", default="",
+                    help="sub_e,d_top,grid_per_sm,level_threads[,q_drop] (skips the autotuner)")
     ap.add_argument("--sampler-traj", type=int, default=64, help="forced trajectories of the M=800 sampler run (0: skip)")
     ap.add_argument("--batched-req", type=int, default=1024, help="requests of the uneven batch (of 4096; 0: skip)")
     ap.add_argument("--served-req", type=int, default=48, help="requests of the served stream (0: skip)")
@@ -407,8 +410,7 @@ def main():
     st = gbs.build_state(ctx, st_p.U, st_p.r, st_p.eta)
     complex_basis = args.basis == "complex"
     if args.tuning:
-        se, dt, gr, lt = (int(x) for x in args.tuning.split(","))
-        ctx.set_tuning(args.prec, args.basis, se, dt, gr, lt)
+        ctx.set_tuning(args.prec, args.basis, *(int(x) for x in args.tuning.split(",")))
         tune_report = []
     else:
         tune_report = ctx.autotune(args.prec, args.basis, min(args.N, 22)) if not args.no_autotune else []
@@ -416,7 +418,7 @@ def main():
     Q = {("fp64", False): 5, ("fp64", True): 4, ("dd", False): 4, ("dd", True): 3, ("td", False): 3,
          ("td", True): 2, ("fp32", False): 5, ("fp32", True): 4, ("fx", False): 3,
          ("fxw", False): 3}[(args.prec, complex_basis)]
-    Q = min(Q, args.N)
+    Q = max(1, min(Q - tuning["q_drop"], args.N))
     q_root = min(args.N, Q + tuning["sub_e"])
     depth = args.N - q_root
     leaf_flops = (2 ** depth) * tree_flops(q_root, complex_basis)

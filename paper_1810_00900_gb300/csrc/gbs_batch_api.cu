@@ -394,6 +394,7 @@ extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, cha
   const int tops[] = {6, 8, 10};
   const int grids[] = {0, 8};
   const long long lts[] = {1LL << 17, 1LL << 19};
+  for (int qd = 0; qd < 2; ++qd)
   for (int se : subs)
     for (int dt : tops)
       for (int gr : grids)
@@ -403,6 +404,7 @@ extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, cha
           cand.d_top = dt;
           cand.leaf_grid_per_sm = gr;
           cand.level_threads = lt;
+          cand.q_drop = qd;
           ctx->tune[prec][real ? 1 : 0] = cand;
           float ms_best = 1e30f;
           for (int rep_i = 0; rep_i < 3; ++rep_i) {
@@ -417,9 +419,11 @@ extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, cha
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep_i > 0 && ms < ms_best) ms_best = ms;  // the first run warms up
           }
-          char buf[160];
-          snprintf(buf, sizeof buf, "%s{\"sub_e\":%d,\"d_top\":%d,\"grid_per_sm\":%d,\"level_threads\":%lld,\"ms\":%.4f}",
-                   rep.size() > 1 ? "," : "", se, dt, gr, lt, ms_best);
+          char buf[192];
+          snprintf(buf, sizeof buf,
+                   "%s{\"sub_e\":%d,\"d_top\":%d,\"grid_per_sm\":%d,\"level_threads\":%lld,\"q_drop\":%d,"
+                   "\"ms\":%.4f}",
+                   rep.size() > 1 ? "," : "", se, dt, gr, lt, qd, ms_best);
           rep += buf;
           if (ms_best < best_ms) {
             best_ms = ms_best;
@@ -440,21 +444,22 @@ done:
 }
 
 extern "C" gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub_e, int* d_top, int* grid_per_sm,
-                                     long long* level_threads) {
+                                     long long* level_threads, int* q_drop) {
   if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FXW) return GBS_EINVAL;
   const BatchTune& t = ctx->tune[prec][basis != GBS_BASIS_COMPLEX ? 1 : 0];
   if (sub_e) *sub_e = t.sub_e;
   if (d_top) *d_top = t.d_top;
   if (grid_per_sm) *grid_per_sm = t.leaf_grid_per_sm;
   if (level_threads) *level_threads = t.level_threads;
+  if (q_drop) *q_drop = t.q_drop;
   return GBS_OK;
 }
 
 extern "C" gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_top, int grid_per_sm,
-                                     long long level_threads) {
+                                     long long level_threads, int q_drop) {
   if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FXW || sub_e < 0 || sub_e > 7 ||
       (sub_e > 0 && sub_e < 5) || d_top < 0 ||
-      d_top > 16 || grid_per_sm < 0 || level_threads < 1)
+      d_top > 16 || grid_per_sm < 0 || level_threads < 1 || q_drop < 0 || q_drop > 2)
     return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
   BatchTune& t = ctx->tune[prec][basis != GBS_BASIS_COMPLEX ? 1 : 0];
@@ -462,6 +467,7 @@ extern "C" gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_
   t.d_top = d_top;
   t.leaf_grid_per_sm = grid_per_sm;
   t.level_threads = level_threads;
+  t.q_drop = q_drop;
   return GBS_OK;
 }
 

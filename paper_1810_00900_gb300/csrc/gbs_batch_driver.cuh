@@ -36,7 +36,7 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
   for (int t = 0; t < ntrees; ++t) {
     const int n = trees[t].n;
     if (n < 1 || n > 40) return set_error(ctx, GBS_EINVAL, "batch tree size out of range");
-    Q[t] = std::min(n, QMAX);
+    Q[t] = std::max(1, std::min(n, QMAX - tune.q_drop));
     qroot[t] = std::min(n, Q[t] + sub_e);
     depth[t] = n - qroot[t];  // levels above the leaf / subtree roots
     dtop[t] = std::min(depth[t], tune.d_top);
@@ -143,9 +143,10 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
   Partial<Red>* parts2 = parts + parts_total;
 
   // ---------------- top
+  // The opt-in limit is set whatever the size: the kernels' static shared
+  // memory (reduction scratch) counts against the default 48 KB as well.
   const size_t smem_top = (size_t)(sym(2 * nmax) + 4 * nmax) * sizeof(E);
-  if (smem_top > 48 * 1024 &&
-      (st = check_cuda(ctx, cudaFuncSetAttribute(batch_top_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((st = check_cuda(ctx, cudaFuncSetAttribute(batch_top_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem_top),
                        "top smem")))
     return st;
@@ -183,8 +184,7 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
   case QQ:                                                                                                      \
     if constexpr (QQ <= QMAX) {                                                                                 \
       if (sub_e > 0) {                                                                                          \
-        if (smem_sub > 48 * 1024 &&                                                                             \
-            (st = check_cuda(ctx,                                                                               \
+        if ((st = check_cuda(ctx,                                                                               \
                              cudaFuncSetAttribute(batch_subtree_kernel<E, QQ>,                                  \
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sub), \
                              "subtree smem")))                                                                  \

@@ -26,6 +26,8 @@ struct BatchTune {
   long long level_threads = 1LL << 18;  // target threads per breadth-first level launch
   int leaf_grid_per_sm = 0;             // 0: one CTA per work unit; k > 0: persistent, k CTAs per SM
   int sub_e = 5;                        // levels each subtree CTA expands in shared memory (0: plain leaf)
+  int q_drop = 0;                       // register depth-first levels below the variant's maximum (fewer
+                                        // registers per thread, more warps per SM)
 };
 
 // Device memory obtained by the library, accounted against the context budget.
