@@ -114,14 +114,20 @@ class ClockSampler:
 
 
 def dist_setup():
+    """One process per GPU (torchrun environment).  The replicas share nothing on the
+    data path; the process group only carries the barrier and the max-over-ranks time
+    (NCCL on GPUs, gloo where there is none)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     return ws, rank, local
 
 
@@ -136,9 +142,25 @@ def allreduce_max(ws, x: float, local: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda:%d" % local)
+    dev = "cuda:%d" % local if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def captured_traffic(args, tuning):
+    """DRAM bytes (read + write) per launch of the dominant kernel from the ncu capture summarised in
+    profiles/batch_subtree_kernel_fp64_real_n24.md, when this run launches that same kernel shape
+    (FP64 real basis, N = 24, 6 shared-memory levels, full register depth, one CTA per node);
+    None otherwise."""
+    same = (args.prec == "fp64" and args.basis == "real" and args.N == 24 and tuning["sub_e"] == 6
+            and tuning["q_drop"] == 0 and tuning["grid_per_sm"] == 0)
+    return 16742400 + 0 if same else None
+
+
+def whole_job_rate(ws: int, units_per_rank: float, seconds_max: float) -> float:
+    """Units all replicas processed divided by the slowest replica's time (weak scaling)."""
+    return ws * units_per_rank / seconds_max
 
 
 def cpu_oracle_rate(n_sample: int):
@@ -172,7 +194,7 @@ def sampler_block(ctx, gbs, gi, n_traj, ws, local):
     pats, p0, stats, status = gbs.sample(ctx, st, n_traj, seed=2, N_post=20, forced_clicks=forced, want_p0=True)
     dt = allreduce_max(ws, time.perf_counter() - t0, local)
     st.free()
-    return {"metric": "M=800,N=20 samples/s", "value": ws * n_traj / dt, "unit": "samples/s",
+    return {"metric": "M=800,N=20 samples/s", "value": whole_job_rate(ws, n_traj, dt), "unit": "samples/s",
             "seconds": dt, "trajectories": n_traj, "steps_evaluated": stats["steps"],
             "escalations": stats["escalations"], "uncertified_steps": stats["uncertified"],
             "gpu_launches": ctx.launch_count - l0,
@@ -459,7 +481,7 @@ def main():
     dev_ms = sum(a.elapsed_time(b) for a, b in ev)
     dev_ms = allreduce_max(ws, dev_ms, local)
     terms = float(2 ** args.N)
-    value = ws * args.steps * terms / (dev_ms * 1e-3)
+    value = whole_job_rate(ws, args.steps * terms, dev_ms * 1e-3)
     leaf_avg_s = leaf_ms / max(leaf_n, 1) * 1e-3
     achieved = leaf_flops / leaf_avg_s / 1e12
     peak = peak_gflops / 1e3
@@ -480,7 +502,7 @@ def main():
         pr = gbs.torontonian(ctx, s2, modes, args.prec, args.basis)
         s2.free()
     e2e_s = allreduce_max(ws, time.perf_counter() - t0, local)
-    e2e_value = ws * args.steps * terms / e2e_s
+    e2e_value = whole_job_rate(ws, args.steps * terms, e2e_s)
     h2d = st_p.M * st_p.M * 16 + st_p.M * 8 + modes.nbytes
     d2h = 8 * 16  # the probability record
 
@@ -502,7 +524,8 @@ def main():
             "bound": "alu", "kernel": kernel_name,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "peak_source": "FP64 DFMA-chain kernel measured in this run (gbs_measure_fp64_peak)",
-            "traffic": None, "flops_per_launch": leaf_flops, "leaf_ms_avg": leaf_avg_s * 1e3,
+            "traffic": captured_traffic(args, tuning), "traffic_unit": "bytes per launch",
+            "flops_per_launch": leaf_flops, "leaf_ms_avg": leaf_avg_s * 1e3,
             "step_flops": total_flops,
             "step_tflops": total_flops * args.steps / (dev_ms * 1e-3) / 1e12,
         },
