@@ -8,9 +8,8 @@
 // least significant) read as X * 2^(-32 (L-2)): fx = fxn<7> has 160 fraction
 // bits, fxw = fxn<8> 192, both a range of +-2^63.  Additions are exact (one
 // carry-chained instruction per limb); a product keeps the columns at and
-// above the fraction point of the exact 2L-limb product (partial products
-// a_i b_j with i + j >= L - 4), which leaves an error of at most two units of
-// the last place, biased low.
+// above the fraction point of the exact 2L-limb product, which leaves an error
+// of at most 2L units of the last place, biased low.
 //
 // Inside the tree every value stays in range when the caller has checked it:
 // entries are bounded by the largest eigenvalue of the root, pivot
@@ -98,15 +97,17 @@ GBS_HD fxn<L> fx_half(const fxn<L>& a) {
 }
 
 // ---------------------------------------------------------------- product --
-// Window of the unsigned product: columns F - 1 (a guard column whose only use
-// is its carry) to F + L - 1, F = L - 2.  Low and high halves of the partial
-// products are summed in two arrays; in either array the carry out of row i
-// lands in a column that no earlier row has reached, so one add captures it.
-// The two's-complement correction subtracts b (resp. a) shifted by L limbs
-// when a (resp. b) is negative.
+// Window of the unsigned product: columns F to F + L - 1 (F = L - 2 fraction
+// limbs).  Low halves of the partial products a_i b_j with i + j >= F and high
+// halves with i + j >= F - 1 are summed in two arrays; in either array the
+// carry out of row i lands in a column that no earlier row has reached, so one
+// add captures it.  The low halves of column F - 1 and everything below are
+// dropped: at most 2L units of the last place, always toward -inf.  The
+// two's-complement correction subtracts b (resp. a) shifted by L limbs when a
+// (resp. b) is negative.
 template <int L>
 GBS_HD fxn<L> operator*(const fxn<L>& a, const fxn<L>& b) {
-  constexpr int F = L - 2, W = L + 1, C0 = F - 1;  // C0: column of word 0
+  constexpr int F = L - 2, W = L, C0 = F;  // C0: column of word 0
   uint32_t lo[W], hi[W];
 #pragma unroll
   for (int k = 0; k < W; ++k) lo[k] = hi[k] = 0u;
@@ -134,10 +135,10 @@ GBS_HD fxn<L> operator*(const fxn<L>& a, const fxn<L>& b) {
     }
   }
   fxn<L> r;
-  (void)add_cc(lo[0], hi[0]);
+  r.w[0] = add_cc(lo[0], hi[0]);
 #pragma unroll
-  for (int k = 0; k < L - 1; ++k) r.w[k] = addc_cc(lo[k + 1], hi[k + 1]);
-  r.w[L - 1] = addc(lo[L], hi[L]);
+  for (int k = 1; k < L - 1; ++k) r.w[k] = addc_cc(lo[k], hi[k]);
+  r.w[L - 1] = addc(lo[L - 1], hi[L - 1]);
   // signed correction: result limbs S .. L-1 (column L and up) minus masked limbs
   constexpr int S = L - F;
   const uint32_t ma = (uint32_t)((int32_t)a.w[L - 1] >> 31), mb = (uint32_t)((int32_t)b.w[L - 1] >> 31);
