@@ -395,7 +395,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default="",
-                    help="sub_e,d_top,grid_per_sm,level_threads[,q_drop] (skips the autotuner)")
+                    help="sub_e,d_top,grid_per_sm,level_threads[,q_drop[,mid_e]] (skips the autotuner)")
     ap.add_argument("--sampler-traj", type=int, default=64, help="forced trajectories of the M=800 sampler run (0: skip)")
     ap.add_argument("--batched-req", type=int, default=1024, help="requests of the uneven batch (of 4096; 0: skip)")
     ap.add_argument("--served-req", type=int, default=48, help="requests of the served stream (0: skip)")

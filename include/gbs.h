@@ -298,16 +298,19 @@ gbs_status gbs_server_stats_get(gbs_ctx* ctx, gbs_server_stats* out);
  *   level_threads  target threads per breadth-first level launch (sets how
  *                  many rows of a node one thread updates);
  *   q_drop         0..2: register depth-first levels below the variant's
- *                  maximum (fewer registers per thread, more warps per SM).
+ *                  maximum (fewer registers per thread, more warps per SM);
+ *   mid_e          0..8: levels each first-kernel CTA goes on expanding in
+ *                  shared memory after its prefix (replacing that many
+ *                  breadth-first level launches; reduced to fit 200 KB).
  * gbs_autotune times candidate shapes on a synthetic n-mode tree (6 <= n <= 28)
  * on the context stream and keeps the fastest for later calls; report (may be
  * NULL) receives the timings as a JSON array, truncated to report_len bytes.
  * The paper has no counterpart (its Titan runs used MPI + OpenMP, Sec. III). */
 gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, char* report, size_t report_len);
 gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub_e, int* d_top, int* grid_per_sm,
-                          long long* level_threads, int* q_drop);
+                          long long* level_threads, int* q_drop, int* mid_e);
 gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_top, int grid_per_sm,
-                          long long level_threads, int q_drop);
+                          long long level_threads, int q_drop, int mid_e);
 
 /* Signed subset sum of an explicit matrix, the enumeration alone:
  *   tor = sum over Z subset {0..n-1} of (-1)^(n-|Z|) det(G_Z)^(-1/2)

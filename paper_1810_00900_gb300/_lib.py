@@ -111,9 +111,9 @@ def load() -> ctypes.CDLL:
         "gbs_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_char_p,
                                         ctypes.c_size_t]),
         "gbs_get_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _ip, _ip, _ip,
-                                          ctypes.POINTER(ctypes.c_longlong), _ip]),
+                                          ctypes.POINTER(ctypes.c_longlong), _ip, _ip]),
         "gbs_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                          ctypes.c_int, ctypes.c_longlong, ctypes.c_int]),
+                                          ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_int]),
         "gbs_sample": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _ip,
                                       ctypes.c_int, ctypes.POINTER(ctypes.c_uint8), _dp,
                                       ctypes.POINTER(gbs_sample_stats)]),
@@ -205,17 +205,17 @@ class Context:
         return json.loads(buf.value.decode() or "[]")
 
     def tuning(self, prec: str = "fp64", basis: str = "real") -> dict:
-        a, b, c, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        a, b, c, e, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         d = ctypes.c_longlong()
         self.check(self.L.gbs_get_tuning(self.h, PREC[prec], BASIS[basis], ctypes.byref(a), ctypes.byref(b),
-                                         ctypes.byref(c), ctypes.byref(d), ctypes.byref(e)))
+                                         ctypes.byref(c), ctypes.byref(d), ctypes.byref(e), ctypes.byref(f)))
         return {"sub_e": a.value, "d_top": b.value, "grid_per_sm": c.value, "level_threads": d.value,
-                "q_drop": e.value}
+                "q_drop": e.value, "mid_e": f.value}
 
     def set_tuning(self, prec: str = "fp64", basis: str = "real", sub_e: int = 5, d_top: int = 10,
-                   grid_per_sm: int = 0, level_threads: int = 1 << 18, q_drop: int = 0):
+                   grid_per_sm: int = 0, level_threads: int = 1 << 18, q_drop: int = 0, mid_e: int = 0):
         self.check(self.L.gbs_set_tuning(self.h, PREC[prec], BASIS[basis], sub_e, d_top, grid_per_sm,
-                                         level_threads, q_drop))
+                                         level_threads, q_drop, mid_e))
 
     def kernel_time(self):
         ms = ctypes.c_double()

@@ -28,9 +28,10 @@ namespace gbs {
 struct TopSeg {
   long long block_begin;  // first CTA of this tree
   long long root_off;     // first packed root entry of the tree
-  long long out_base;     // entry offset of its depth-dtop nodes (SoA, count = 2^dtop)
+  long long out_base;     // entry offset of its output nodes (SoA, count = 2^(dtop + emid))
   long long s_base;       // offset of their s values
   int n, dtop, tree, buf;  // buf: level buffer (0/1) receiving the nodes
+  int emid, pad;           // levels each CTA then expands in shared memory before writing
 };
 
 struct LevelSeg {
@@ -70,12 +71,71 @@ __device__ __forceinline__ void untri(int e, int& a, int& b) {
   b = e - r * (r + 1) / 2;
 }
 
+// Breadth-first expansion of `levels` tree levels inside one CTA: src holds
+// `nodes` nodes with q undecided modes (entry-major: entry e of node t at
+// src[e * nodes + t]) and ssrc their s.  Each level replaces node t by its
+// exclude child 2t and include child 2t + 1; on return src/ssrc point at the
+// last level and nodes/q describe it.  Scratch: pm10, pq00, pq11, pg hold one
+// value per node of the level being split.
+template <class E>
+__device__ __forceinline__ void smem_expand(E*& src, E*& dst, typename real_of<E>::type*& ssrc,
+                                            typename real_of<E>::type*& sdst, E* pm10,
+                                            typename real_of<E>::type* pq00, typename real_of<E>::type* pq11,
+                                            typename real_of<E>::type* pg, int& nodes, int& q, int levels,
+                                            bool& bad) {
+  typedef typename real_of<E>::type T;
+  const int nthr = blockDim.x;
+  for (int lvl = 0; lvl < levels; ++lvl) {
+    for (int t = threadIdx.x; t < nodes; t += nthr) {
+      const T p00 = re_of(src[tri(0, 0) * nodes + t]);
+      const T p11 = re_of(src[tri(1, 1) * nodes + t]);
+      const E p10 = src[tri(1, 0) * nodes + t];
+      const T det = p00 * p11 - norm2(p10);
+      bad |= !is_pos(det);
+      const T g = rsqrt_(det);
+      const T inv = g * g;
+      pg[t] = g;
+      pq00[t] = p00 * inv;
+      pq11[t] = p11 * inv;
+      pm10[t] = neg_(scale_(p10, inv));
+      sdst[2 * t] = ssrc[t];
+      sdst[2 * t + 1] = ssrc[t] * g;
+    }
+    __syncthreads();
+    const int rows = 2 * q - 2;
+    const int n2 = 2 * nodes;
+    for (int task = threadIdx.x; task < nodes * rows; task += nthr) {
+      const int t = task % nodes, a = task / nodes;
+#define SRC(i, j) src[tri(i, j) * nodes + t]
+      const E u0 = SRC(a + 2, 0), u1 = SRC(a + 2, 1);
+      const E m10 = pm10[t];
+      const E L0 = lin2(u0, pq11[t], u1, m10);
+      const E L1 = lin2(u1, pq00[t], u0, conj_(m10));
+      for (int b = 0; b < a; ++b) {
+        const E x = SRC(a + 2, b + 2);
+        dst[tri(a, b) * n2 + 2 * t] = x;
+        dst[tri(a, b) * n2 + 2 * t + 1] = fms_conj(fms_conj(x, L0, SRC(b + 2, 0)), L1, SRC(b + 2, 1));
+      }
+      const E x = SRC(a + 2, a + 2);
+      dst[tri(a, a) * n2 + 2 * t] = x;
+      dst[tri(a, a) * n2 + 2 * t + 1] = fms_conj_re(fms_conj_re(x, L0, u0), L1, u1);
+#undef SRC
+    }
+    __syncthreads();
+    E* tmp = src; src = dst; dst = tmp;
+    T* ts = ssrc; ssrc = sdst; sdst = ts;
+    nodes = n2;
+    --q;
+  }
+}
+
 // ---------------------------------------------------------------- top ----
 template <class E>
 __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
                                  const typename root_src<E>::type* __restrict__ roots, E* __restrict__ buf0,
                                  E* __restrict__ buf1, typename real_of<E>::type* __restrict__ s0,
-                                 typename real_of<E>::type* __restrict__ s1, int* __restrict__ status) {
+                                 typename real_of<E>::type* __restrict__ s1, int* __restrict__ status, int capA,
+                                 int capB, int mid_off, int ncap) {
   typedef typename real_of<E>::type T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   E* C = reinterpret_cast<E*>(smem_raw);
@@ -122,18 +182,45 @@ __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
   }
   const int o = 2 * sg.dtop;
   const int dq = d - o;
-  const long long cnt = 1LL << sg.dtop;
   E* out = sg.buf ? buf1 : buf0;
   T* sout = sg.buf ? s1 : s0;
-  for (int e = threadIdx.x; e < sym(dq); e += blockDim.x) {
-    int a, b;
-    untri(e, a, b);
-    out[sg.out_base + (long long)e * cnt + node] = C[tri(a + o, b + o)];
+  if (sg.emid == 0) {
+    const long long cnt = 1LL << sg.dtop;
+    for (int e = threadIdx.x; e < sym(dq); e += blockDim.x) {
+      int a, b;
+      untri(e, a, b);
+      out[sg.out_base + (long long)e * cnt + node] = C[tri(a + o, b + o)];
+    }
+    if (threadIdx.x == 0) sout[sg.s_base + node] = s;
+  } else {
+    // The node goes on breadth first in shared memory for emid more levels and
+    // writes its 2^emid descendants (node index (node << emid) | t at that depth).
+    E* src = reinterpret_cast<E*>(smem_raw) + mid_off;
+    E* dst = src + capA;
+    E* pm10 = dst + capB;
+    T* ssrc = reinterpret_cast<T*>(pm10 + ncap);
+    T* sdst = ssrc + ncap;
+    T* pq00 = sdst + ncap;
+    T* pq11 = pq00 + ncap;
+    T* pg = pq11 + ncap;
+    for (int e = threadIdx.x; e < sym(dq); e += blockDim.x) {
+      int a, b;
+      untri(e, a, b);
+      src[e] = C[tri(a + o, b + o)];
+    }
+    if (threadIdx.x == 0) ssrc[0] = s;
+    __syncthreads();
+    int nodes = 1, q = sg.n - sg.dtop;
+    smem_expand<E>(src, dst, ssrc, sdst, pm10, pq00, pq11, pg, nodes, q, sg.emid, bad);
+    const long long cnt = 1LL << (sg.dtop + sg.emid);
+    const long long first = node << sg.emid;
+    for (int i = threadIdx.x; i < sym(2 * q) * nodes; i += blockDim.x) {
+      const int e = i / nodes, t = i - e * nodes;
+      out[sg.out_base + (long long)e * cnt + first + t] = src[i];
+    }
+    for (int t = threadIdx.x; t < nodes; t += blockDim.x) sout[sg.s_base + first + t] = ssrc[t];
   }
-  if (threadIdx.x == 0) {
-    sout[sg.s_base + node] = s;
-    if (bad) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
-  }
+  if (bad) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
 }
 
 // ---------------------------------------------------------------- level --
@@ -271,48 +358,7 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
     T* sdst = sB;
     int nodes = 1;
     bool bad = false;
-    for (int lvl = 0; lvl < sg.e_levels; ++lvl) {
-      for (int t = threadIdx.x; t < nodes; t += nthr) {
-        const T p00 = re_of(src[tri(0, 0) * nodes + t]);
-        const T p11 = re_of(src[tri(1, 1) * nodes + t]);
-        const E p10 = src[tri(1, 0) * nodes + t];
-        const T det = p00 * p11 - norm2(p10);
-        bad |= !is_pos(det);
-        const T g = rsqrt_(det);
-        const T inv = g * g;
-        pg[t] = g;
-        pq00[t] = p00 * inv;
-        pq11[t] = p11 * inv;
-        pm10[t] = neg_(scale_(p10, inv));
-        sdst[2 * t] = ssrc[t];
-        sdst[2 * t + 1] = ssrc[t] * g;
-      }
-      __syncthreads();
-      const int rows = 2 * q - 2;
-      const int n2 = 2 * nodes;
-      for (int task = threadIdx.x; task < nodes * rows; task += nthr) {
-        const int t = task % nodes, a = task / nodes;
-#define SRC(i, j) src[tri(i, j) * nodes + t]
-        const E u0 = SRC(a + 2, 0), u1 = SRC(a + 2, 1);
-        const E m10 = pm10[t];
-        const E L0 = lin2(u0, pq11[t], u1, m10);
-        const E L1 = lin2(u1, pq00[t], u0, conj_(m10));
-        for (int b = 0; b < a; ++b) {
-          const E x = SRC(a + 2, b + 2);
-          dst[tri(a, b) * n2 + 2 * t] = x;
-          dst[tri(a, b) * n2 + 2 * t + 1] = fms_conj(fms_conj(x, L0, SRC(b + 2, 0)), L1, SRC(b + 2, 1));
-        }
-        const E x = SRC(a + 2, a + 2);
-        dst[tri(a, a) * n2 + 2 * t] = x;
-        dst[tri(a, a) * n2 + 2 * t + 1] = fms_conj_re(fms_conj_re(x, L0, u0), L1, u1);
-#undef SRC
-      }
-      __syncthreads();
-      E* tmp = src; src = dst; dst = tmp;
-      T* ts = ssrc; ssrc = sdst; sdst = ts;
-      nodes = n2;
-      --q;
-    }
+    smem_expand<E>(src, dst, ssrc, sdst, pm10, pq00, pq11, pg, nodes, q, sg.e_levels, bad);
     if (bad) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
     Red inc = red_zero<Red>(), exc = red_zero<Red>();
     double asum = 0.0;

@@ -394,6 +394,7 @@ extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, cha
   const int tops[] = {6, 8, 10};
   const int grids[] = {0, 8};
   const long long lts[] = {1LL << 17, 1LL << 19};
+  for (int me = 0; me <= 5; me += 5)
   for (int qd = 0; qd < 2; ++qd)
   for (int se : subs)
     for (int dt : tops)
@@ -405,6 +406,7 @@ extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, cha
           cand.leaf_grid_per_sm = gr;
           cand.level_threads = lt;
           cand.q_drop = qd;
+          cand.mid_e = me;
           ctx->tune[prec][real ? 1 : 0] = cand;
           float ms_best = 1e30f;
           for (int rep_i = 0; rep_i < 3; ++rep_i) {
@@ -422,8 +424,8 @@ extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, cha
           char buf[192];
           snprintf(buf, sizeof buf,
                    "%s{\"sub_e\":%d,\"d_top\":%d,\"grid_per_sm\":%d,\"level_threads\":%lld,\"q_drop\":%d,"
-                   "\"ms\":%.4f}",
-                   rep.size() > 1 ? "," : "", se, dt, gr, lt, qd, ms_best);
+                   "\"mid_e\":%d,\"ms\":%.4f}",
+                   rep.size() > 1 ? "," : "", se, dt, gr, lt, qd, me, ms_best);
           rep += buf;
           if (ms_best < best_ms) {
             best_ms = ms_best;
@@ -444,7 +446,7 @@ done:
 }
 
 extern "C" gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub_e, int* d_top, int* grid_per_sm,
-                                     long long* level_threads, int* q_drop) {
+                                     long long* level_threads, int* q_drop, int* mid_e) {
   if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FXW) return GBS_EINVAL;
   const BatchTune& t = ctx->tune[prec][basis != GBS_BASIS_COMPLEX ? 1 : 0];
   if (sub_e) *sub_e = t.sub_e;
@@ -452,14 +454,15 @@ extern "C" gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub
   if (grid_per_sm) *grid_per_sm = t.leaf_grid_per_sm;
   if (level_threads) *level_threads = t.level_threads;
   if (q_drop) *q_drop = t.q_drop;
+  if (mid_e) *mid_e = t.mid_e;
   return GBS_OK;
 }
 
 extern "C" gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_top, int grid_per_sm,
-                                     long long level_threads, int q_drop) {
+                                     long long level_threads, int q_drop, int mid_e) {
   if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FXW || sub_e < 0 || sub_e > 7 ||
       (sub_e > 0 && sub_e < 5) || d_top < 0 ||
-      d_top > 16 || grid_per_sm < 0 || level_threads < 1 || q_drop < 0 || q_drop > 2)
+      d_top > 16 || grid_per_sm < 0 || level_threads < 1 || q_drop < 0 || q_drop > 2 || mid_e < 0 || mid_e > 8)
     return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
   BatchTune& t = ctx->tune[prec][basis != GBS_BASIS_COMPLEX ? 1 : 0];
@@ -468,6 +471,7 @@ extern "C" gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_
   t.leaf_grid_per_sm = grid_per_sm;
   t.level_threads = level_threads;
   t.q_drop = q_drop;
+  t.mid_e = mid_e;
   return GBS_OK;
 }
 

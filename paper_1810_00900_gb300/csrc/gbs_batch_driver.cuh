@@ -29,7 +29,7 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
   if (ntrees <= 0) return GBS_OK;
   const int sub_e = std::max(0, std::min(tune.sub_e, 7));  // levels expanded inside a subtree CTA
   // ---------------- plan
-  std::vector<int> Q(ntrees), depth(ntrees), dtop(ntrees), qroot(ntrees);
+  std::vector<int> Q(ntrees), depth(ntrees), dtop(ntrees), qroot(ntrees), emid(ntrees);
   std::vector<long long> region(ntrees), sreg(ntrees);
   long long region_total = 0, s_total = 0;
   int max_depth = 0, nmax = 0;
@@ -40,6 +40,7 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
     qroot[t] = std::min(n, Q[t] + sub_e);
     depth[t] = n - qroot[t];  // levels above the leaf / subtree roots
     dtop[t] = std::min(depth[t], tune.d_top);
+    emid[t] = std::min(depth[t] - dtop[t], std::max(0, std::min(tune.mid_e, 8)));
     long long biggest = 0;
     for (int l = dtop[t]; l <= depth[t]; ++l)
       biggest = std::max(biggest, (1LL << l) * (long long)sym(2 * (n - l)));
@@ -50,17 +51,43 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
     max_depth = std::max(max_depth, depth[t]);
     nmax = std::max(nmax, n);
   }
+  // Shared memory of the top kernel: the root and its L rows, then, when its
+  // CTAs go on breadth first (emid > 0), two level buffers and per-node
+  // scratch; emid shrinks until that fits in 200 KB.
+  const int mid_off = sym(2 * nmax) + 4 * nmax;
+  int capA_top = 1, capB_top = 1, ncap = 1;
+  size_t smem_top = (size_t)mid_off * sizeof(E);
+  for (int ecap = 8; ecap >= 0; --ecap) {
+    int emax = 0;
+    capA_top = capB_top = 1;
+    for (int t = 0; t < ntrees; ++t) {
+      const int e = std::min(emid[t], ecap);
+      emax = std::max(emax, e);
+      for (int j = 0; j <= e && e > 0; ++j) {
+        const int c = (1 << j) * sym(2 * (trees[t].n - dtop[t] - j));
+        if (j & 1) capB_top = std::max(capB_top, c); else capA_top = std::max(capA_top, c);
+      }
+    }
+    ncap = 1 << emax;
+    smem_top = emax == 0 ? (size_t)mid_off * sizeof(E)
+                         : (size_t)(mid_off + capA_top + capB_top + ncap) * sizeof(E) + 5 * (size_t)ncap * sizeof(T);
+    if (smem_top <= 200 * 1024 || ecap == 0) {
+      for (int t = 0; t < ntrees; ++t) emid[t] = std::min(emid[t], ecap);
+      break;
+    }
+  }
   std::vector<TopSeg> top(ntrees);
   long long top_blocks = 0;
   for (int t = 0; t < ntrees; ++t) {
-    top[t] = TopSeg{top_blocks, trees[t].root_off, region[t], sreg[t], trees[t].n, dtop[t], t, dtop[t] & 1};
+    top[t] = TopSeg{top_blocks, trees[t].root_off, region[t], sreg[t], trees[t].n, dtop[t], t,
+                    (dtop[t] + emid[t]) & 1, emid[t], 0};
     top_blocks += 1LL << dtop[t];
   }
   std::vector<std::vector<LevelSeg>> levels(max_depth);
   std::vector<long long> level_threads(max_depth, 0);
   for (int l = 0; l < max_depth; ++l) {
     for (int t = 0; t < ntrees; ++t) {
-      if (l < dtop[t] || l >= depth[t]) continue;
+      if (l < dtop[t] + emid[t] || l >= depth[t]) continue;
       const long long count = 1LL << l;
       const int q = trees[t].n - l;
       const int rows = 2 * q - 2;
@@ -145,14 +172,13 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
   // ---------------- top
   // The opt-in limit is set whatever the size: the kernels' static shared
   // memory (reduction scratch) counts against the default 48 KB as well.
-  const size_t smem_top = (size_t)(sym(2 * nmax) + 4 * nmax) * sizeof(E);
   if ((st = check_cuda(ctx, cudaFuncSetAttribute(batch_top_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem_top),
                        "top smem")))
     return st;
   batch_top_kernel<E><<<(unsigned)top_blocks, tune.top_threads, smem_top, s>>>(
       (const TopSeg*)(plan + o_top), ntrees, (const typename root_src<E>::type*)roots_dev, buf[0], buf[1], sb[0], sb[1],
-      status_dev);
+      status_dev, capA_top, capB_top, mid_off, ncap);
   count_launch(ctx);
   // ---------------- breadth-first levels
   for (int l = 0; l < max_depth; ++l) {

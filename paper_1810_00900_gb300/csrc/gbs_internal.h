@@ -28,6 +28,7 @@ struct BatchTune {
   int sub_e = 5;                        // levels each subtree CTA expands in shared memory (0: plain leaf)
   int q_drop = 0;                       // register depth-first levels below the variant's maximum (fewer
                                         // registers per thread, more warps per SM)
+  int mid_e = 0;                        // levels each top CTA expands in shared memory after its prefix
 };
 
 // Device memory obtained by the library, accounted against the context budget.

@@ -28,19 +28,19 @@ def test_launch_shapes_agree(ctx):
     for sub_e in (0, 5, 6, 7):
         for d_top in (0, 4, 10):
             for grid in (0, 2):
-                for q_drop in (0, 1):
-                    ctx.set_tuning("dd", "real", sub_e, d_top, grid, 1 << 17, q_drop)
+                for q_drop, mid_e in ((0, 0), (1, 0), (0, 5), (1, 3)):
+                    ctx.set_tuning("dd", "real", sub_e, d_top, grid, 1 << 17, q_drop, mid_e)
                     _, _, tor, a = gbs.subset_sum(ctx, H, "real", "dd")
                     err = abs(float(frac3(tor) - ref.to_fraction()))
-                    assert err <= 8 * 17 * 2.0 ** -102 * ref_abs, (sub_e, d_top, grid, q_drop, err)
+                    assert err <= 8 * 17 * 2.0 ** -102 * ref_abs, (sub_e, d_top, grid, q_drop, mid_e, err)
                     seen.append(tor)
     ctx.set_tuning("dd", "real", 5, 10, 0, 1 << 18)
     # the fixed-point sums are exact and their reduction order fixed: every shape gives the same bits
     fx_seen = set()
     for sub_e in (0, 6):
         for d_top in (0, 8):
-            for q_drop in (0, 1, 2):
-                ctx.set_tuning("fx", "real", sub_e, d_top, 8, 1 << 17, q_drop)
+            for q_drop, mid_e in ((0, 0), (1, 0), (2, 0), (0, 5), (1, 2)):
+                ctx.set_tuning("fx", "real", sub_e, d_top, 8, 1 << 17, q_drop, mid_e)
                 _, _, tor, _ = gbs.subset_sum(ctx, H, "real", "fx")
                 fx_seen.add(tuple(tor))
                 assert abs(float(frac3(tor) - ref.to_fraction())) <= 8 * 17 * 2.0 ** -140 * ref_abs
@@ -53,5 +53,5 @@ def test_autotune_picks_a_candidate(ctx):
     assert len(rep) >= 8 and all(r["ms"] > 0 for r in rep)
     best = min(rep, key=lambda r: r["ms"])
     t = ctx.tuning("fp64", "real")
-    assert (t["sub_e"], t["d_top"], t["grid_per_sm"], t["q_drop"]) == (best["sub_e"], best["d_top"],
-                                                                       best["grid_per_sm"], best["q_drop"])
+    keys = ("sub_e", "d_top", "grid_per_sm", "q_drop", "mid_e")
+    assert tuple(t[k] for k in keys) == tuple(best[k] for k in keys)
