@@ -151,11 +151,11 @@ def allreduce_max(ws, x: float, local: int) -> float:
 def captured_traffic(args, tuning):
     """DRAM bytes (read + write) per launch of the dominant kernel from the ncu capture summarised in
     profiles/batch_subtree_kernel_fp64_real_n24.md, when this run launches that same kernel shape
-    (FP64 real basis, N = 24, 6 shared-memory levels, full register depth, one CTA per node);
-    None otherwise."""
+    (FP64 real basis, N = 24, 6 shared-memory levels, full register depth; the same bytes were
+    counted with one CTA per node and with the persistent grid); None otherwise."""
     same = (args.prec == "fp64" and args.basis == "real" and args.N == 24 and tuning["sub_e"] == 6
-            and tuning["q_drop"] == 0 and tuning["grid_per_sm"] == 0)
-    return 16742400 + 0 if same else None
+            and tuning["q_drop"] == 0 and tuning["grid_per_sm"] in (0, 8))
+    return 16741888 + 0 if same else None
 
 
 def whole_job_rate(ws: int, units_per_rank: float, seconds_max: float) -> float:
@@ -295,7 +295,7 @@ def batched_block(ctx, gbs, gi, n_req, n_err):
                         "eta~U[0.25,1.0], Haar seeded per request" % n_req}
 
 
-def served_block(ctx, gbs, gi, n_req, max_attempts):
+def served_block(ctx, gbs, gi, n_req, max_attempts, width):
     """The served dense-subgraph stream: Poisson arrivals (200/s) of postselected sampling jobs on
     graph-encoded states; latency percentiles of the request loop beside the same requests served
     one at a time by direct calls (whose results must be identical)."""
@@ -307,7 +307,7 @@ def served_block(ctx, gbs, gi, n_req, max_attempts):
             sp = gi.graph_state(graphs[g], 2.0 * N, eta)
             cache[(g, eta, N)] = gbs.build_state(ctx, sp.U, sp.r, sp.eta)
         sts.append(cache[(g, eta, N)])
-    srv = gbs.Server(ctx, arena_bytes=8 << 30, max_active=64)
+    srv = gbs.Server(ctx, arena_bytes=8 << 30, max_active=64, attempt_width=width)
     t0 = time.perf_counter()
     tickets = []
     for i, (a, (g, eta, N)) in enumerate(zip(arrivals, reqs)):
@@ -347,7 +347,7 @@ def served_block(ctx, gbs, gi, n_req, max_attempts):
             "loop_busy_fraction": stats["busy_s"] / max(stats["wall_s"], 1e-9),
             "one_at_a_time": {"samples_per_s": ok / max(free_at, 1e-9), "p50_s": float(np.percentile(lat1, 50)),
                               "p99_s": float(np.percentile(lat1, 99)), "busy_seconds": float(sum(svc))},
-            "results_identical_to_one_at_a_time": bool(same),
+            "results_identical_to_one_at_a_time": bool(same), "attempt_width": width,
             "workload": "Poisson arrivals at 200/s; ER graphs n in [100,200] p=0.1 with a planted 20-vertex "
                         "p=0.9 part; c for mean photon number 2N; eta in {1,0.5,0.25}; one sample postselected "
                         "on N in [8,20] per request, up to %d attempts" % max_attempts}
@@ -400,6 +400,8 @@ def main():
     ap.add_argument("--batched-req", type=int, default=1024, help="requests of the uneven batch (of 4096; 0: skip)")
     ap.add_argument("--served-req", type=int, default=48, help="requests of the served stream (0: skip)")
     ap.add_argument("--served-attempts", type=int, default=24, help="postselection attempts per served request")
+    ap.add_argument("--served-width", type=int, default=8,
+                    help="postselection attempts a served request runs at once (1: one after another)")
     ap.add_argument("--walltime-m", default="10,12,14,16,18,20",
                     help="click counts of the worst-case walltime rows (paper Table II sizes; empty: skip)")
     args = ap.parse_args()
@@ -541,7 +543,7 @@ def main():
     if args.batched_req > 0:
         line["batched"] = batched_block(ctx, gbs, gi, args.batched_req, 48)
     if args.served_req > 0:
-        line["served"] = served_block(ctx, gbs, gi, args.served_req, args.served_attempts)
+        line["served"] = served_block(ctx, gbs, gi, args.served_req, args.served_attempts, args.served_width)
     if args.walltime_m:
         line["walltime"] = walltime_block(ctx, gbs, gi, [int(x) for x in args.walltime_m.split(",")])
     if rank == 0 and not args.no_cpu_baseline:

@@ -265,15 +265,19 @@ typedef struct {
 /* Start the context's request loop: a worker thread that admits submitted
  * requests in arrival order while their device footprint fits an arena of
  * arena_bytes (allocated now; a sampling request needs 32 M^2 bytes plus about
- * 32 M, a probability request only the shared tree workspace) and at most
- * max_active sampling requests run at once.  Each loop iteration evaluates all
- * newly admitted probability requests as one batch and advances every active
- * sampling request by one measured mode, all their subset trees batched
- * together, so late arrivals join running work at the next step.  A result is
- * bitwise the same alone and in any mix.  While the loop runs, direct calls on
- * the same context still work (they interleave with loop iterations).
+ * 32 M per attempt slot, a probability request only the shared tree
+ * workspace) and at most max_active sampling requests run at once.  Each loop
+ * iteration evaluates all newly admitted probability requests as one batch and
+ * advances every running sampling attempt by one measured mode, all their
+ * subset trees batched together, so late arrivals join running work at the
+ * next step.  attempt_width (1..64): postselection attempts a sampling request
+ * runs at once (attempts a, a+1, ... on separate trajectories); its result is
+ * still the lowest accepted attempt, the one attempts run one after another
+ * give, so a result is bitwise the same alone, in any mix and at any width.
+ * While the loop runs, direct calls on the same context still work (they
+ * interleave with loop iterations).
  * The paper has no counterpart (its runs were single jobs, Sec. III-IV). */
-gbs_status gbs_server_start(gbs_ctx* ctx, size_t arena_bytes, int max_active);
+gbs_status gbs_server_start(gbs_ctx* ctx, size_t arena_bytes, int max_active, int attempt_width);
 /* Stop the loop (waits for the current iteration); unpolled results are dropped. */
 gbs_status gbs_server_stop(gbs_ctx* ctx);
 /* Queue a request; *ticket identifies it.  Errors: GBS_EINVAL (loop not running,

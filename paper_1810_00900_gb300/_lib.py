@@ -117,7 +117,7 @@ def load() -> ctypes.CDLL:
         "gbs_sample": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _ip,
                                       ctypes.c_int, ctypes.POINTER(ctypes.c_uint8), _dp,
                                       ctypes.POINTER(gbs_sample_stats)]),
-        "gbs_server_start": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.c_int]),
+        "gbs_server_start": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
         "gbs_server_stop": (ctypes.c_int, [_vp]),
         "gbs_submit": (ctypes.c_int, [_vp, ctypes.POINTER(gbs_request), ctypes.POINTER(ctypes.c_uint64)]),
         "gbs_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(gbs_result), ctypes.c_int64]),
@@ -356,9 +356,9 @@ def sample(ctx: Context, st: State, n_samples: int, seed: int, N_post: int = 0, 
 class Server:
     """The context's request loop (gbs_server_start / gbs_submit / gbs_poll)."""
 
-    def __init__(self, ctx: Context, arena_bytes: int = 4 << 30, max_active: int = 64):
+    def __init__(self, ctx: Context, arena_bytes: int = 4 << 30, max_active: int = 64, attempt_width: int = 1):
         self.ctx = ctx
-        ctx.check(ctx.L.gbs_server_start(ctx.h, int(arena_bytes), int(max_active)))
+        ctx.check(ctx.L.gbs_server_start(ctx.h, int(arena_bytes), int(max_active), int(attempt_width)))
         self._keep = {}
 
     def submit_prob(self, st: State, modes, prec: str = "auto", basis: str = "auto", rel_tol: float = 0.0) -> int:

@@ -39,6 +39,11 @@ namespace {
 
 using clock_t_ = std::chrono::steady_clock;
 
+// A sampling request runs up to `width` postselection attempts at once, one per
+// trajectory slot.  outcome[a] records attempt a (0 unknown, 1 rejected,
+// 2 accepted with its clicks); the request's result is the lowest accepted
+// attempt once every attempt below it is known to be rejected -- exactly what
+// attempts run one after the other give.
 struct Req {
   uint64_t ticket = 0;
   gbs_request r{};
@@ -46,7 +51,11 @@ struct Req {
   clock_t_::time_point t_submit, t_admit;
   size_t footprint = 0;
   long long arena_off = -1;
-  Trajectory traj;
+  std::vector<Trajectory> slots;
+  std::vector<int> slot_attempt;  // attempt running in each slot, -1 = idle
+  std::vector<signed char> outcome;
+  std::map<int, std::vector<int>> accepted_clicks;
+  int next_attempt = 0;
   bool admitted = false, done = false;
   gbs_result res{};
 };
@@ -108,6 +117,7 @@ struct Server {
   DevBuf arena;
   ArenaAlloc alloc;
   int max_active = 64;
+  int width = 1;  // postselection attempts run at once per sampling request
   int max_prob_batch = 4096;
   gbs_status fatal = GBS_OK;
   // statistics
@@ -117,8 +127,32 @@ struct Server {
   clock_t_::time_point t_start;
 };
 
-size_t footprint_of(const gbs_request& r) {
-  return r.kind == GBS_REQ_SAMPLE ? traj_bytes(r.state->M) : 0;
+int width_of(const Server* sv, const gbs_request& r) {
+  return std::max(1, std::min(sv->width, r.max_attempts));
+}
+
+size_t footprint_of(const Server* sv, const gbs_request& r) {
+  return r.kind == GBS_REQ_SAMPLE ? (size_t)width_of(sv, r) * ((traj_bytes(r.state->M) + 255) / 256 * 256) : 0;
+}
+
+// Start attempt `a` of request q in slot k.
+gbs_status start_attempt(gbs_ctx* ctx, Req* q, int k, int a) {
+  Trajectory& tj = q->slots[k];
+  tj.seed = q->r.seed;
+  tj.sample = q->r.sample_index;
+  tj.attempt = a;
+  tj.N_post = q->r.N;
+  tj.want_p0 = false;
+  q->slot_attempt[k] = a;
+  return traj_start(ctx, tj);
+}
+
+// Lowest attempt whose outcome is not "rejected": its index and outcome.
+int first_open(const Req* q, int* oc) {
+  int a = 0;
+  while (a < (int)q->outcome.size() && q->outcome[a] == 1) ++a;
+  *oc = a < (int)q->outcome.size() ? q->outcome[a] : 1;
+  return a;
 }
 
 void finish(Server* sv, Req* q, gbs_status st) {
@@ -154,7 +188,7 @@ void worker_loop(Server* sv) {
           probs.push_back(q);
         } else {
           if ((int)sv->active.size() >= sv->max_active) break;
-          const long long off = sv->alloc.take(q->footprint);
+          const long long off = sv->alloc.take(q->footprint);  // all attempt slots in one block
           if (off < 0) break;  // wait for memory to free up (first in, first out)
           q->arena_off = off;
           sv->active.push_back(q);
@@ -197,19 +231,22 @@ void worker_loop(Server* sv) {
           }
         }
       }
-      // 2. sampling: start the new ones, advance everyone by one mode
+      // 2. sampling: start the new ones, advance every running attempt by one mode
       for (Req* q : fresh) {
-        Trajectory& tj = q->traj;
-        traj_bind(tj, const_cast<gbs_state*>(q->r.state), (unsigned char*)sv->arena.ptr + q->arena_off);
-        tj.seed = q->r.seed;
-        tj.sample = q->r.sample_index;
-        tj.attempt = 0;
-        tj.N_post = q->r.N;
-        tj.want_p0 = false;
-        const gbs_status st = traj_start(ctx, tj);
+        const int w = width_of(sv, q->r);
+        const size_t stride = (traj_bytes(q->r.state->M) + 255) / 256 * 256;
+        q->slots.assign(w, Trajectory());
+        q->slot_attempt.assign(w, -1);
+        q->outcome.assign(q->r.max_attempts, 0);
+        gbs_status st = GBS_OK;
+        for (int k = 0; k < w && !st; ++k) {
+          traj_bind(q->slots[k], const_cast<gbs_state*>(q->r.state),
+                    (unsigned char*)sv->arena.ptr + q->arena_off + k * stride);
+          st = start_attempt(ctx, q, k, q->next_attempt++);
+        }
         if (st) {
           sv->fatal = st;
-          tj.state = -1;  // failed: completed below with the error
+          for (auto& tj : q->slots) tj.state = -1;  // failed: completed below with the error
           finished.push_back(q);
           fin_status.push_back(st);
         }
@@ -217,36 +254,68 @@ void worker_loop(Server* sv) {
       // one advance per precision setting (requests normally all use AUTO)
       std::map<int, std::vector<Req*>> by_prec;
       for (Req* q : active)
-        if (q->traj.state == Trajectory::kRunning) by_prec[q->r.prec].push_back(q);
+        for (auto& tj : q->slots)
+          if (tj.state == Trajectory::kRunning) {
+            by_prec[q->r.prec].push_back(q);
+            break;
+          }
       for (auto& kv : by_prec) {
         std::vector<Trajectory*> tjs;
-        for (Req* q : kv.second) tjs.push_back(&q->traj);
+        for (Req* q : kv.second)
+          for (auto& tj : q->slots)
+            if (tj.state == Trajectory::kRunning) tjs.push_back(&tj);
         gbs_sample_stats stt{};
         const gbs_status st = sampler_advance(ctx, tjs, kv.first, stt);
         if (st) sv->fatal = st;
         for (Req* q : kv.second) {
-          Trajectory& tj = q->traj;
           if (st) {
             finished.push_back(q);
             fin_status.push_back(st);
-          } else if (tj.state == Trajectory::kDone) {
-            q->res.n_clicks = (int)tj.S.size();
-            for (int c = 0; c < (int)tj.S.size() && c < 64; ++c) q->res.clicks[c] = tj.S[c];
-            q->res.attempts = tj.attempt + 1;
+            continue;
+          }
+          // record the attempts that ended in this step
+          for (size_t k = 0; k < q->slots.size(); ++k) {
+            Trajectory& tj = q->slots[k];
+            const int a = q->slot_attempt[k];
+            if (a < 0 || tj.state == Trajectory::kRunning) continue;
+            if (tj.state == Trajectory::kDone) {
+              q->outcome[a] = 2;
+              q->accepted_clicks[a] = tj.S;
+            } else {
+              q->outcome[a] = 1;
+            }
+            q->slot_attempt[k] = -1;
+          }
+          int oc = 0;
+          const int a0 = first_open(q, &oc);
+          if (a0 == (int)q->outcome.size()) {  // every attempt rejected
+            q->res.attempts = a0;
+            finished.push_back(q);
+            fin_status.push_back(GBS_EREJECT);
+            continue;
+          }
+          if (oc == 2) {  // the lowest attempt not rejected was accepted
+            const std::vector<int>& S = q->accepted_clicks[a0];
+            q->res.n_clicks = (int)S.size();
+            for (int c = 0; c < (int)S.size() && c < 64; ++c) q->res.clicks[c] = S[c];
+            q->res.attempts = a0 + 1;
             finished.push_back(q);
             fin_status.push_back(GBS_OK);
-          } else if (tj.state == Trajectory::kRejected) {
-            if (tj.attempt + 1 < q->r.max_attempts) {
-              tj.attempt++;
-              if (traj_start(ctx, tj)) {
-                finished.push_back(q);
-                fin_status.push_back(GBS_ECUDA);
-              }
-            } else {
-              q->res.attempts = tj.attempt + 1;
-              finished.push_back(q);
-              fin_status.push_back(GBS_EREJECT);
+            continue;
+          }
+          // attempts above an accepted one can no longer matter: stop them
+          const int best = q->accepted_clicks.empty() ? (int)q->outcome.size() : q->accepted_clicks.begin()->first;
+          gbs_status e2 = GBS_OK;
+          for (size_t k = 0; k < q->slots.size() && !e2; ++k) {
+            if (q->slot_attempt[k] > best) {
+              q->slots[k].state = Trajectory::kRejected;
+              q->slot_attempt[k] = -1;
             }
+            if (q->slot_attempt[k] < 0 && q->next_attempt < best) e2 = start_attempt(ctx, q, (int)k, q->next_attempt++);
+          }
+          if (e2) {
+            finished.push_back(q);
+            fin_status.push_back(e2);
           }
         }
       }
@@ -324,12 +393,13 @@ using namespace gbs;
 
 extern "C" {
 
-gbs_status gbs_server_start(gbs_ctx* ctx, size_t arena_bytes, int max_active) {
-  if (!ctx || arena_bytes == 0 || max_active < 1) return GBS_EINVAL;
+gbs_status gbs_server_start(gbs_ctx* ctx, size_t arena_bytes, int max_active, int attempt_width) {
+  if (!ctx || arena_bytes == 0 || max_active < 1 || attempt_width < 1 || attempt_width > 64) return GBS_EINVAL;
   if (ctx->server) return set_error(ctx, GBS_EINVAL, "request loop already running");
   Server* sv = new Server();
   sv->ctx = ctx;
   sv->max_active = max_active;
+  sv->width = attempt_width;
   {
     std::lock_guard<std::mutex> g(ctx->mu);
     cudaSetDevice(ctx->device);
@@ -366,7 +436,7 @@ gbs_status gbs_submit(gbs_ctx* ctx, const gbs_request* req, uint64_t* ticket) {
     return e;
   }
   q->r.modes = nullptr;
-  q->footprint = footprint_of(q->r);
+  q->footprint = footprint_of(sv, q->r);
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (q->footprint > sv->alloc.cap) {

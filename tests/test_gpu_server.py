@@ -68,20 +68,23 @@ def test_served_equals_direct_in_a_mix(ctx):
             assert res["prob"].p == d.p and res["prob"].tor == d.tor
 
 
-def test_postselected_sampling_served_matches_oracle(ctx):
+@pytest.mark.parametrize("width", [1, 4, 16])
+def test_postselected_sampling_served_matches_oracle(ctx, width):
+    # attempts run `width` at a time; the result is still the lowest accepted attempt
     M = 8
     U = gi.haar_unitary(M, 33)
     r = gi.uniform_range(33, "squeezing", M, 0.4, 0.9)
     st = gbs.build_state(ctx, U, r, 0.7)
     Sig = oracle.sigma(oracle.covariance(U, r, 0.7))
-    srv = gbs.Server(ctx, arena_bytes=16 << 20, max_active=4)
+    srv = gbs.Server(ctx, arena_bytes=64 << 20, max_active=4, attempt_width=width)
     ts = [srv.submit_sample(st, seed=9, sample_index=i, N_post=3, max_attempts=40) for i in range(6)]
+    ts.append(srv.submit_sample(st, seed=9, sample_index=6, N_post=7, max_attempts=3))  # exhausts its attempts
     res = [srv.poll(t, timeout_s=120) for t in ts]
     srv.stop()
     for i, rr in enumerate(res):
-        ref = oracle.sample_chain(Sig, 9, sample=i, N_post=3, max_attempts=40)
+        ref = oracle.sample_chain(Sig, 9, sample=i, N_post=3 if i < 6 else 7, max_attempts=40 if i < 6 else 3)
         if ref["pattern"] is None:
-            assert rr["status"] == _lib.EREJECT
+            assert rr["status"] == _lib.EREJECT and rr["attempts"] == (40 if i < 6 else 3)
         else:
             assert rr["status"] == 0 and rr["clicks"] == np.nonzero(ref["pattern"])[0].tolist()
             assert rr["attempts"] == ref["attempts"]
