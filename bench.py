@@ -353,6 +353,47 @@ def served_block(ctx, gbs, gi, n_req, max_attempts, width):
                         "on N in [8,20] per request, up to %d attempts" % max_attempts}
 
 
+def subgraph_density(A, nodes):
+    """Edges inside the vertex set over the number of vertex pairs."""
+    nodes = np.asarray(nodes)
+    k = len(nodes)
+    return float(A[np.ix_(nodes, nodes)].sum() / 2.0) / (k * (k - 1) / 2.0) if k > 1 else 0.0
+
+
+def dense_subgraph_block(ctx, gbs, gi, n_samples):
+    """The paper's application (Sec. IV): random search for a dense subgraph with GBS samples of the
+    graph-encoded state against uniformly random vertex sets of the same size, on a 100-vertex
+    Erdos-Renyi graph (p = 0.1) with a planted 20-vertex part (p = 0.9)."""
+    A = gi.planted_graph(100, 11)
+    planted = set(gi.planted_vertices(100, 11).tolist())
+    rows = []
+    for N in (8, 12, 16):
+        sp = gi.graph_state(A, 2.0 * N, 1.0)
+        st = gbs.build_state(ctx, sp.U, sp.r, sp.eta)
+        t0 = time.perf_counter()
+        pats, _, stats, status = gbs.sample(ctx, st, n_samples, seed=N, N_post=N, max_attempts=256, check=False)
+        dt = time.perf_counter() - t0
+        st.free()
+        ok = [np.nonzero(p)[0] for p in pats if p[0] != 0xFF]
+        uni = gi.uniform_subsets(100, N, n_samples, seed=N)
+        d_gbs = [subgraph_density(A, s) for s in ok]
+        d_uni = [subgraph_density(A, s) for s in uni]
+        rows.append({"N": N, "samples": len(ok), "seconds": dt, "samples_per_s": len(ok) / dt,
+                     "attempts_rejected": stats["rejections"],
+                     "mean_density_gbs": float(np.mean(d_gbs)) if d_gbs else None,
+                     "mean_density_uniform": float(np.mean(d_uni)),
+                     "max_density_gbs": float(np.max(d_gbs)) if d_gbs else None,
+                     "max_density_uniform": float(np.max(d_uni)),
+                     "mean_planted_fraction_gbs": float(np.mean([len(planted & set(s.tolist())) / N for s in ok]))
+                     if ok else None,
+                     "mean_planted_fraction_uniform": float(np.mean([len(planted & set(s.tolist())) / N
+                                                                     for s in uni]))})
+    return {"metric": "dense-subgraph random search: GBS samples vs uniform subsets", "rows": rows,
+            "workload": "ER(100, 0.1) with a planted 20-vertex part at 0.9 (seed 11); state with mean photon "
+                        "number 2N, no loss; %d samples postselected on N clicks per row, the same number of "
+                        "uniform N-subsets" % n_samples}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -402,6 +443,8 @@ def main():
     ap.add_argument("--served-attempts", type=int, default=24, help="postselection attempts per served request")
     ap.add_argument("--served-width", type=int, default=8,
                     help="postselection attempts a served request runs at once (1: one after another)")
+    ap.add_argument("--dense-samples", type=int, default=128,
+                    help="GBS samples per row of the dense-subgraph search (0: skip)")
     ap.add_argument("--walltime-m", default="10,12,14,16,18,20",
                     help="click counts of the worst-case walltime rows (paper Table II sizes; empty: skip)")
     args = ap.parse_args()
@@ -546,6 +589,8 @@ def main():
         line["served"] = served_block(ctx, gbs, gi, args.served_req, args.served_attempts, args.served_width)
     if args.walltime_m:
         line["walltime"] = walltime_block(ctx, gbs, gi, [int(x) for x in args.walltime_m.split(",")])
+    if args.dense_samples > 0:
+        line["dense_subgraph"] = dense_subgraph_block(ctx, gbs, gi, args.dense_samples)
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()

@@ -42,6 +42,7 @@ STREAMS = {
     "clicks": 6,
     "arrivals": 7,
     "requests": 8,
+    "uniform-subsets": 9,
 }
 
 
@@ -232,6 +233,16 @@ def planted_graph(n: int, seed: int, p: float = 0.1, k: int = 20, q: float = 0.9
     A = np.triu(A, 1)
     A = A + A.T
     return A
+
+
+def planted_vertices(n: int, seed: int, k: int = 20) -> np.ndarray:
+    """The k vertices planted_graph(n, seed, k=k) made dense."""
+    return random_modes(n, k, seed, stream="graph", start=n * n)
+
+
+def uniform_subsets(n: int, size: int, count: int, seed: int) -> np.ndarray:
+    """count subsets of `size` vertices out of n, uniformly at random (the baseline of random search)."""
+    return np.array([random_modes(n, size, seed, stream="uniform-subsets", start=i * size) for i in range(count)])
 
 
 def graph_state(A: np.ndarray, mean_photons: float, eta: float = 1.0) -> StateParams:

@@ -58,7 +58,7 @@ def build(verbose: bool = False, ptxas_info: bool = False, jobs: int | None = No
         r = subprocess.run(cmd, capture_output=True, text=True)
         return cmd, r
 
-    with cf.ThreadPoolExecutor(max_workers=jobs or min(8, os.cpu_count() or 4)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=jobs or min(16, os.cpu_count() or 4)) as ex:
         for cmd, r in ex.map(run, cmds):
             if verbose or ptxas_info or r.returncode:
                 sys.stderr.write(" ".join(cmd[-3:]) + "\n" + r.stdout + r.stderr)
