@@ -324,7 +324,7 @@ gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_to
  * symmetric positive definite (only the lower triangle is read).
  * inc, exc, tor: caller-owned double[3] each (may be NULL), unevaluated sums.
  * prec must not be GBS_PREC_AUTO; GBS_PREC_FX / FXW need the real basis and a matrix
- * whose eigenvalues lie in [2^-10, 2^10] with (1 + 1/lambda_min)^n < 2^60
+ * whose eigenvalues lie in [2^-8, 64] with (1 + 1/lambda_min)^n < 2^60
  * (checked on the host; otherwise GBS_EPRECISION).
  * Errors: GBS_EINVAL, GBS_ENOTPD, GBS_EPRECISION, GBS_ECUDA. */
 gbs_status gbs_subset_sum(gbs_ctx* ctx, int n, const double* G, int basis, int prec, double* inc, double* exc,

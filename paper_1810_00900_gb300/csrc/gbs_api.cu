@@ -317,7 +317,8 @@ gbs_status gbs_subset_sum(gbs_ctx* ctx, int n, const double* G, int basis, int p
   const bool real = basis != GBS_BASIS_COMPLEX;
   if (prec == GBS_PREC_FX || prec == GBS_PREC_FXW) {
     double lmin = 0.0, lmax = 0.0;
-    if (!real || !sym_eig_range(G, 2 * n, lmin, lmax) || !(lmin >= 0x1p-10 && lmax <= 1024.0) ||
+    // entries and their scaled pivot inverses stay below 2^31: eigenvalues in [2^-8, 64]
+    if (!real || !sym_eig_range(G, 2 * n, lmin, lmax) || !(lmin >= 0x1p-8 && lmax <= 64.0) ||
         !(n * std::log2(1.0 + 1.0 / lmin) < 60.0))
       return set_error(ctx, GBS_EPRECISION, "gbs_subset_sum: matrix outside the fixed-point range");
   }

@@ -78,12 +78,13 @@ __device__ __forceinline__ void untri(int e, int& a, int& b) {
 // last level and nodes/q describe it.  Scratch: pm10, pq00, pq11, pg hold one
 // value per node of the level being split.
 template <class E>
-__device__ __forceinline__ void smem_expand(E*& src, E*& dst, typename real_of<E>::type*& ssrc,
-                                            typename real_of<E>::type*& sdst, E* pm10,
+__device__ __forceinline__ void smem_expand(E*& src, E*& dst, typename scale_of<E>::type*& ssrc,
+                                            typename scale_of<E>::type*& sdst, E* pm10,
                                             typename real_of<E>::type* pq00, typename real_of<E>::type* pq11,
                                             typename real_of<E>::type* pg, int& nodes, int& q, int levels,
                                             bool& bad) {
   typedef typename real_of<E>::type T;
+  typedef typename scale_of<E>::type S;
   const int nthr = blockDim.x;
   for (int lvl = 0; lvl < levels; ++lvl) {
     for (int t = threadIdx.x; t < nodes; t += nthr) {
@@ -123,7 +124,7 @@ __device__ __forceinline__ void smem_expand(E*& src, E*& dst, typename real_of<E
     }
     __syncthreads();
     E* tmp = src; src = dst; dst = tmp;
-    T* ts = ssrc; ssrc = sdst; sdst = ts;
+    S* ts = ssrc; ssrc = sdst; sdst = ts;
     nodes = n2;
     --q;
   }
@@ -133,10 +134,11 @@ __device__ __forceinline__ void smem_expand(E*& src, E*& dst, typename real_of<E
 template <class E>
 __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
                                  const typename root_src<E>::type* __restrict__ roots, E* __restrict__ buf0,
-                                 E* __restrict__ buf1, typename real_of<E>::type* __restrict__ s0,
-                                 typename real_of<E>::type* __restrict__ s1, int* __restrict__ status, int capA,
+                                 E* __restrict__ buf1, typename scale_of<E>::type* __restrict__ s0,
+                                 typename scale_of<E>::type* __restrict__ s1, int* __restrict__ status, int capA,
                                  int capB, int mid_off, int ncap) {
   typedef typename real_of<E>::type T;
+  typedef typename scale_of<E>::type S;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   E* C = reinterpret_cast<E*>(smem_raw);
   const TopSeg sg = segs[find_seg(segs, nseg, (long long)blockIdx.x, &TopSeg::block_begin)];
@@ -145,7 +147,7 @@ __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
   for (int i = threadIdx.x; i < sym(d); i += blockDim.x) C[i] = conv_entry<E>(roots[sg.root_off + i]);
   __syncthreads();
   E* Lrow = C + sym(d);  // L0 of row a at Lrow[2a], L1 at Lrow[2a+1]
-  T s = from_double<T>(1.0);
+  S s = from_double<S>(1.0);
   bool bad = false;
   for (int i = 0; i < sg.dtop; ++i) {
     if (!((node >> (sg.dtop - 1 - i)) & 1)) continue;  // excluded: the view just moves on
@@ -183,7 +185,7 @@ __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
   const int o = 2 * sg.dtop;
   const int dq = d - o;
   E* out = sg.buf ? buf1 : buf0;
-  T* sout = sg.buf ? s1 : s0;
+  S* sout = sg.buf ? s1 : s0;
   if (sg.emid == 0) {
     const long long cnt = 1LL << sg.dtop;
     for (int e = threadIdx.x; e < sym(dq); e += blockDim.x) {
@@ -198,9 +200,9 @@ __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
     E* src = reinterpret_cast<E*>(smem_raw) + mid_off;
     E* dst = src + capA;
     E* pm10 = dst + capB;
-    T* ssrc = reinterpret_cast<T*>(pm10 + ncap);
-    T* sdst = ssrc + ncap;
-    T* pq00 = sdst + ncap;
+    S* ssrc = reinterpret_cast<S*>(pm10 + ncap);
+    S* sdst = ssrc + ncap;
+    T* pq00 = reinterpret_cast<T*>(sdst + ncap);
     T* pq11 = pq00 + ncap;
     T* pg = pq11 + ncap;
     for (int e = threadIdx.x; e < sym(dq); e += blockDim.x) {
@@ -226,8 +228,8 @@ __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
 // ---------------------------------------------------------------- level --
 template <class E>
 __global__ void batch_level_kernel(const LevelSeg* __restrict__ segs, int nseg, long long total,
-                                   const E* __restrict__ in, const typename real_of<E>::type* __restrict__ sin,
-                                   E* __restrict__ out, typename real_of<E>::type* __restrict__ sout,
+                                   const E* __restrict__ in, const typename scale_of<E>::type* __restrict__ sin,
+                                   E* __restrict__ out, typename scale_of<E>::type* __restrict__ sout,
                                    int* __restrict__ status) {
   typedef typename real_of<E>::type T;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -272,7 +274,7 @@ __global__ void batch_level_kernel(const LevelSeg* __restrict__ segs, int nseg, 
     chi[(long long)tri(a, a) * c2 + 2 * node + 1] = v;
   }
   if (grp == 0) {
-    const T s = sin[sg.s_in + node];
+    const typename scale_of<E>::type s = sin[sg.s_in + node];
     sout[sg.s_out + 2 * node] = s;
     sout[sg.s_out + 2 * node + 1] = s * g;
   }
@@ -284,8 +286,8 @@ template <class E, int Q>
 __global__ void __launch_bounds__(128) batch_leaf_kernel(const LeafSeg* __restrict__ segs, int nseg,
                                                          long long total_blocks, const E* __restrict__ buf0,
                                                          const E* __restrict__ buf1,
-                                                         const typename real_of<E>::type* __restrict__ s0,
-                                                         const typename real_of<E>::type* __restrict__ s1,
+                                                         const typename scale_of<E>::type* __restrict__ s0,
+                                                         const typename scale_of<E>::type* __restrict__ s1,
                                                          Partial<typename acc_traits<typename real_of<E>::type>::Red>* parts,
                                                          int* __restrict__ status) {
   typedef typename real_of<E>::type T;
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(128) batch_leaf_kernel(const LeafSeg* __restri
       E c[sym(2 * Q)];
 #pragma unroll
       for (int e = 0; e < sym(2 * Q); ++e) c[e] = nodes[(long long)e * sg.count + node];
-      const T s = (sg.buf ? s1 : s0)[sg.s_base + node];
+      const typename scale_of<E>::type s = (sg.buf ? s1 : s0)[sg.s_base + node];
       if (!subtree_sums<E, Q>(c, s, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
       if ((sg.depth - __popcll((unsigned long long)node)) & 1) {
         inc = red_neg(inc);
@@ -328,8 +330,8 @@ struct SubSeg {
 template <class E, int Q>
 __global__ void __launch_bounds__(128) batch_subtree_kernel(
     const SubSeg* __restrict__ segs, int nseg, long long total_blocks, const E* __restrict__ buf0,
-    const E* __restrict__ buf1, const typename real_of<E>::type* __restrict__ s0,
-    const typename real_of<E>::type* __restrict__ s1, int capA, int capB,
+    const E* __restrict__ buf1, const typename scale_of<E>::type* __restrict__ s0,
+    const typename scale_of<E>::type* __restrict__ s1, int capA, int capB,
     Partial<typename acc_traits<typename real_of<E>::type>::Red>* parts, int* __restrict__ status) {
   typedef typename real_of<E>::type T;
   typedef typename acc_traits<T>::Acc Acc;
@@ -339,9 +341,10 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
   E* bufA = reinterpret_cast<E*>(smem_raw);
   E* bufB = bufA + capA;
   E* pm10 = bufB + capB;                           // per node of the current level
-  T* sA = reinterpret_cast<T*>(pm10 + nthr);       // s of the current level
-  T* sB = sA + nthr;
-  T* pq00 = sB + nthr;
+  typedef typename scale_of<E>::type S;
+  S* sA = reinterpret_cast<S*>(pm10 + nthr);       // s of the current level
+  S* sB = sA + nthr;
+  T* pq00 = reinterpret_cast<T*>(sB + nthr);
   T* pq11 = pq00 + nthr;
   T* pg = pq11 + nthr;
   for (long long vb = blockIdx.x; vb < total_blocks; vb += gridDim.x) {
@@ -354,8 +357,8 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
     __syncthreads();
     E* src = bufA;
     E* dst = bufB;
-    T* ssrc = sA;
-    T* sdst = sB;
+    S* ssrc = sA;
+    S* sdst = sB;
     int nodes = 1;
     bool bad = false;
     smem_expand<E>(src, dst, ssrc, sdst, pm10, pq00, pq11, pg, nodes, q, sg.e_levels, bad);
@@ -367,7 +370,7 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
       E c[sym(2 * Q)];
 #pragma unroll
       for (int e = 0; e < sym(2 * Q); ++e) c[e] = src[e * nodes + t];
-      const T sv = ssrc[t];
+      const S sv = ssrc[t];
       if (!subtree_sums<E, Q>(c, sv, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
       const unsigned long long gnode = ((unsigned long long)root << sg.e_levels) | (unsigned long long)t;
       if ((sg.depth_leaf - __popcll(gnode)) & 1) {

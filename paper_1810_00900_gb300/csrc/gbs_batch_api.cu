@@ -50,8 +50,10 @@ const BatchTune& batch_tune_for(gbs_ctx* ctx, int prec, bool real) {
 
 // Every value of a tree over n modes of (Sigma^-1)_S fits the fixed-point
 // range: Sigma >= I/2 bounds the entries by 2, the pivot determinants lie in
-// [1/sigma_max^2, 4], each included pivot multiplies s by at most sigma_max,
-// and the sums are bounded by (1 + sigma_max)^n.
+// [1/sigma_max^2, 4] (so the scaled pivot inverses and the products formed with
+// them stay below 2^23, inside the entries' 31-bit integer part), each included
+// pivot multiplies s by at most sigma_max, and the sums are bounded by
+// (1 + sigma_max)^n (inside the 63-bit integer part of s and the sums).
 bool fx_ok_inverse(const gbs_state* st, int n) {
   const double sm = st->sigma_max;
   return sm > 0.0 && sm <= 1024.0 && n * std::log2(1.0 + sm) < 60.0;

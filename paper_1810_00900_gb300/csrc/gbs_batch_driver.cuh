@@ -25,6 +25,7 @@ template <class E, int QMAX>
 gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const void* roots_dev, TreeOut* outs_dev,
                      int* status_dev, const BatchTune& tune) {
   typedef typename real_of<E>::type T;
+  typedef typename scale_of<E>::type S;
   typedef typename acc_traits<T>::Red Red;
   if (ntrees <= 0) return GBS_OK;
   const int sub_e = std::max(0, std::min(tune.sub_e, 7));  // levels expanded inside a subtree CTA
@@ -70,7 +71,8 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
     }
     ncap = 1 << emax;
     smem_top = emax == 0 ? (size_t)mid_off * sizeof(E)
-                         : (size_t)(mid_off + capA_top + capB_top + ncap) * sizeof(E) + 5 * (size_t)ncap * sizeof(T);
+                         : (size_t)(mid_off + capA_top + capB_top + ncap) * sizeof(E) +
+                               (size_t)ncap * (2 * sizeof(S) + 3 * sizeof(T));
     if (smem_top <= 200 * 1024 || ecap == 0) {
       for (int t = 0; t < ntrees; ++t) emid[t] = std::min(emid[t], ecap);
       break;
@@ -148,8 +150,8 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
   gbs_status st;
   if ((st = dev_reserve(ctx, ctx->lvl[0], (size_t)region_total * sizeof(E))) ||
       (st = dev_reserve(ctx, ctx->lvl[1], (size_t)region_total * sizeof(E))) ||
-      (st = dev_reserve(ctx, ctx->sbuf[0], (size_t)s_total * sizeof(T))) ||
-      (st = dev_reserve(ctx, ctx->sbuf[1], (size_t)s_total * sizeof(T))) ||
+      (st = dev_reserve(ctx, ctx->sbuf[0], (size_t)s_total * sizeof(S))) ||
+      (st = dev_reserve(ctx, ctx->sbuf[1], (size_t)s_total * sizeof(S))) ||
       (st = dev_reserve(ctx, ctx->partials, (size_t)(parts_total + chunks.size()) * sizeof(Partial<Red>))))
     return st;
   Blob blob;
@@ -165,7 +167,7 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
 
   cudaStream_t s = ctx->stream;
   E* buf[2] = {(E*)ctx->lvl[0].ptr, (E*)ctx->lvl[1].ptr};
-  T* sb[2] = {(T*)ctx->sbuf[0].ptr, (T*)ctx->sbuf[1].ptr};
+  S* sb[2] = {(S*)ctx->sbuf[0].ptr, (S*)ctx->sbuf[1].ptr};
   Partial<Red>* parts = (Partial<Red>*)ctx->partials.ptr;
   Partial<Red>* parts2 = parts + parts_total;
 
@@ -197,7 +199,7 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
     }
     cudaEventRecord(ctx->leaf_timer.start, s);
   }
-  const size_t smem_sub = (size_t)(capA + capB + nthr) * sizeof(E) + 5 * (size_t)nthr * sizeof(T);
+  const size_t smem_sub = (size_t)(capA + capB + nthr) * sizeof(E) + (size_t)nthr * (2 * sizeof(S) + 3 * sizeof(T));
   for (int qv = QMAX; qv >= 1; --qv) {
     const long long nb = grp_blocks[qv];
     if (nb == 0) continue;

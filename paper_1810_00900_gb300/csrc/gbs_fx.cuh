@@ -1,15 +1,20 @@
-// Fixed-point multiword numbers on the integer pipe: the "FX" precision.
+// Fixed-point multiword numbers on the integer pipe: the "FX" precisions.
 //
 // The subset tree needs ~160-bit arithmetic once the cancellation ratio passes
 // ~1e20.  Built from FP64 error-free transformations (triple-double) each
 // operation costs ~30 FP64 instructions, and this GPU issues only 2 FP64 FMAs
 // per clock per SM, against ~60 32-bit integer multiply-adds and carry-chained
-// adds.  fxn<L> holds a two's-complement integer X of L 32-bit limbs (limb 0
-// least significant) read as X * 2^(-32 (L-2)): fx = fxn<7> has 160 fraction
-// bits, fxw = fxn<8> 192, both a range of +-2^63.  Additions are exact (one
-// carry-chained instruction per limb); a product keeps the columns at and
-// above the fraction point of the exact 2L-limb product, which leaves an error
-// of at most 2L units of the last place, biased low.
+// adds.  fxn<L, F> holds a two's-complement integer X of L 32-bit limbs (limb 0
+// least significant) read as X * 2^(-32 F).  Two widths serve each precision:
+// the matrix entries and the scalars derived from them (pivots, determinants,
+// inverse square roots) need only 31 integer bits, the running product s of
+// pivot factors and the sums of terms need 63:
+//   FX    entries fx  = fxn<6, 5>, s and sums fxs  = fxn<7, 5>  (160 fraction bits)
+//   FXW   entries fxw = fxn<7, 6>, s and sums fxws = fxn<8, 6>  (192 fraction bits)
+// Additions are exact (one carry-chained instruction per limb); a product
+// keeps the columns at and above the fraction point of the exact 2L-limb
+// product, which leaves an error of at most 2L units of the last place,
+// biased low.
 //
 // Inside the tree every value stays in range when the caller has checked it:
 // entries are bounded by the largest eigenvalue of the root, pivot
@@ -27,13 +32,15 @@
 
 namespace gbs {
 
-// fxn<L>: L limbs, L - 2 of them fraction limbs (range +-2^63 in every width).
-template <int L>
+template <int L, int F>
 struct fxn {
+  static_assert(F >= 3 && L > F, "at least three fraction limbs and one integer limb");
   uint32_t w[L];
 };
-typedef fxn<7> fx;   // 160 fraction bits (GBS_PREC_FX)
-typedef fxn<8> fxw;  // 192 fraction bits (GBS_PREC_FXW)
+typedef fxn<6, 5> fx;    // FX entries
+typedef fxn<7, 5> fxs;   // FX s and sums
+typedef fxn<7, 6> fxw;   // FXW entries
+typedef fxn<8, 6> fxws;  // FXW s and sums
 
 // ------------------------------------------------ carry-chained primitives --
 // The carry flag lives between consecutive volatile asm statements of one
@@ -59,27 +66,27 @@ GBS_HD uint32_t madc_hi_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; GBS
 #undef GBS_ASM2
 
 // ---------------------------------------------------------------- basics --
-template <int L>
-GBS_HD fxn<L> operator+(const fxn<L>& a, const fxn<L>& b) {
-  fxn<L> r;
+template <int L, int F>
+GBS_HD fxn<L, F> operator+(const fxn<L, F>& a, const fxn<L, F>& b) {
+  fxn<L, F> r;
   r.w[0] = add_cc(a.w[0], b.w[0]);
 #pragma unroll
   for (int k = 1; k < L - 1; ++k) r.w[k] = addc_cc(a.w[k], b.w[k]);
   r.w[L - 1] = addc(a.w[L - 1], b.w[L - 1]);
   return r;
 }
-template <int L>
-GBS_HD fxn<L> operator-(const fxn<L>& a, const fxn<L>& b) {
-  fxn<L> r;
+template <int L, int F>
+GBS_HD fxn<L, F> operator-(const fxn<L, F>& a, const fxn<L, F>& b) {
+  fxn<L, F> r;
   r.w[0] = sub_cc(a.w[0], b.w[0]);
 #pragma unroll
   for (int k = 1; k < L - 1; ++k) r.w[k] = subc_cc(a.w[k], b.w[k]);
   r.w[L - 1] = subc(a.w[L - 1], b.w[L - 1]);
   return r;
 }
-template <int L>
-GBS_HD fxn<L> operator-(const fxn<L>& a) {
-  fxn<L> r;
+template <int L, int F>
+GBS_HD fxn<L, F> operator-(const fxn<L, F>& a) {
+  fxn<L, F> r;
   r.w[0] = sub_cc(0u, a.w[0]);
 #pragma unroll
   for (int k = 1; k < L - 1; ++k) r.w[k] = subc_cc(0u, a.w[k]);
@@ -87,27 +94,35 @@ GBS_HD fxn<L> operator-(const fxn<L>& a) {
   return r;
 }
 // x / 2 (arithmetic shift by one bit)
-template <int L>
-GBS_HD fxn<L> fx_half(const fxn<L>& a) {
-  fxn<L> r;
+template <int L, int F>
+GBS_HD fxn<L, F> fx_half(const fxn<L, F>& a) {
+  fxn<L, F> r;
 #pragma unroll
   for (int k = 0; k < L - 1; ++k) r.w[k] = (a.w[k] >> 1) | (a.w[k + 1] << 31);
   r.w[L - 1] = (uint32_t)((int32_t)a.w[L - 1] >> 1);
   return r;
 }
+// The same value with one more integer limb (sign extension).
+template <int L, int F>
+GBS_HD fxn<L + 1, F> fx_widen(const fxn<L, F>& a) {
+  fxn<L + 1, F> r;
+#pragma unroll
+  for (int k = 0; k < L; ++k) r.w[k] = a.w[k];
+  r.w[L] = (uint32_t)((int32_t)a.w[L - 1] >> 31);
+  return r;
+}
 
 // ---------------------------------------------------------------- product --
-// Window of the unsigned product: columns F to F + L - 1 (F = L - 2 fraction
-// limbs).  Low halves of the partial products a_i b_j with i + j >= F and high
-// halves with i + j >= F - 1 are summed in two arrays; in either array the
-// carry out of row i lands in a column that no earlier row has reached, so one
-// add captures it.  The low halves of column F - 1 and everything below are
-// dropped: at most 2L units of the last place, always toward -inf.  The
-// two's-complement correction subtracts b (resp. a) shifted by L limbs when a
-// (resp. b) is negative.
-template <int L>
-GBS_HD fxn<L> operator*(const fxn<L>& a, const fxn<L>& b) {
-  constexpr int F = L - 2, W = L, C0 = F;  // C0: column of word 0
+// Window of the unsigned product: columns F to F + L - 1.  Low halves of the
+// partial products a_i b_j with i + j >= F and high halves with i + j >= F - 1
+// are summed in two arrays; in either array the carry out of row i lands in a
+// column that no earlier row has reached, so one add captures it.  The low
+// halves of column F - 1 and everything below are dropped: at most 2L units of
+// the last place, always toward -inf.  The two's-complement correction
+// subtracts b (resp. a) shifted by L limbs when a (resp. b) is negative.
+template <int L, int F>
+GBS_HD fxn<L, F> operator*(const fxn<L, F>& a, const fxn<L, F>& b) {
+  constexpr int W = L, C0 = F;  // C0: column of word 0
   uint32_t lo[W], hi[W];
 #pragma unroll
   for (int k = 0; k < W; ++k) lo[k] = hi[k] = 0u;
@@ -134,7 +149,7 @@ GBS_HD fxn<L> operator*(const fxn<L>& a, const fxn<L>& b) {
       }
     }
   }
-  fxn<L> r;
+  fxn<L, F> r;
   r.w[0] = add_cc(lo[0], hi[0]);
 #pragma unroll
   for (int k = 1; k < L - 1; ++k) r.w[k] = addc_cc(lo[k], hi[k]);
@@ -142,22 +157,32 @@ GBS_HD fxn<L> operator*(const fxn<L>& a, const fxn<L>& b) {
   // signed correction: result limbs S .. L-1 (column L and up) minus masked limbs
   constexpr int S = L - F;
   const uint32_t ma = (uint32_t)((int32_t)a.w[L - 1] >> 31), mb = (uint32_t)((int32_t)b.w[L - 1] >> 31);
-  r.w[S] = sub_cc(r.w[S], b.w[0] & ma);
+  if constexpr (S == L - 1) {
+    r.w[S] -= (b.w[0] & ma) + (a.w[0] & mb);
+  } else {
+    r.w[S] = sub_cc(r.w[S], b.w[0] & ma);
 #pragma unroll
-  for (int k = S + 1; k < L - 1; ++k) r.w[k] = subc_cc(r.w[k], b.w[k - S] & ma);
-  r.w[L - 1] = subc(r.w[L - 1], b.w[L - 1 - S] & ma);
-  r.w[S] = sub_cc(r.w[S], a.w[0] & mb);
+    for (int k = S + 1; k < L - 1; ++k) r.w[k] = subc_cc(r.w[k], b.w[k - S] & ma);
+    r.w[L - 1] = subc(r.w[L - 1], b.w[L - 1 - S] & ma);
+    r.w[S] = sub_cc(r.w[S], a.w[0] & mb);
 #pragma unroll
-  for (int k = S + 1; k < L - 1; ++k) r.w[k] = subc_cc(r.w[k], a.w[k - S] & mb);
-  r.w[L - 1] = subc(r.w[L - 1], a.w[L - 1 - S] & mb);
+    for (int k = S + 1; k < L - 1; ++k) r.w[k] = subc_cc(r.w[k], a.w[k - S] & mb);
+    r.w[L - 1] = subc(r.w[L - 1], a.w[L - 1 - S] & mb);
+  }
   return r;
+}
+// s * g: the wide scale type times an entry scalar.
+template <int L, int F>
+GBS_HD fxn<L + 1, F> operator*(const fxn<L + 1, F>& a, const fxn<L, F>& b) {
+  return a * fx_widen(b);
 }
 
 // ----------------------------------------------------------- conversions --
-// Exact for |x| < 2^62 down to 2^-(32 (L-2)) (bits below are dropped, toward zero).
-template <int L>
-GBS_HD fxn<L> fx_from_double(double x) {
-  fxn<L> r;
+// Exact while |x| fits the integer limbs, down to 2^-(32 F) (bits below are
+// dropped, toward zero).
+template <int L, int F>
+GBS_HD fxn<L, F> fx_from_double(double x) {
+  fxn<L, F> r;
 #ifdef __CUDA_ARCH__
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
 #else
@@ -166,7 +191,7 @@ GBS_HD fxn<L> fx_from_double(double x) {
 #endif
   const int e = (int)((bits >> 52) & 0x7ff);
   const unsigned long long m = (bits & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
-  const int sh = (e ? e : 1) - 1075 + 32 * (L - 2);  // bit position of m's last bit in X
+  const int sh = (e ? e : 1) - 1075 + 32 * F;  // bit position of m's last bit in X
 #pragma unroll
   for (int k = 0; k < L; ++k) {
     const int s = 32 * k - sh;
@@ -175,82 +200,96 @@ GBS_HD fxn<L> fx_from_double(double x) {
   }
   return (bits >> 63) ? -r : r;
 }
-template <> GBS_HD fx from_double<fx>(double x) { return fx_from_double<7>(x); }
-template <> GBS_HD fxw from_double<fxw>(double x) { return fx_from_double<8>(x); }
+template <> GBS_HD fx from_double<fx>(double x) { return fx_from_double<6, 5>(x); }
+template <> GBS_HD fxs from_double<fxs>(double x) { return fx_from_double<7, 5>(x); }
+template <> GBS_HD fxw from_double<fxw>(double x) { return fx_from_double<7, 6>(x); }
+template <> GBS_HD fxws from_double<fxws>(double x) { return fx_from_double<8, 6>(x); }
 
 // Nearest-ish double (a few units of the last place).
-template <int L>
-GBS_HD double to_double(const fxn<L>& a) {
+template <int L, int F>
+GBS_HD double to_double(const fxn<L, F>& a) {
   double v = (double)(int32_t)a.w[L - 1];
 #pragma unroll
   for (int k = L - 2; k >= 0; --k) v = fma(v, 4294967296.0, (double)a.w[k]);
-  return v * (L == 7 ? 0x1p-160 : 0x1p-192);
+  return v * (F == 5 ? 0x1p-160 : 0x1p-192);
 }
-static_assert(sizeof(fx) == 28 && sizeof(fxw) == 32, "fx widths");
+static_assert(sizeof(fx) == 24 && sizeof(fxs) == 28 && sizeof(fxw) == 28 && sizeof(fxws) == 32, "fx widths");
 
 // ------------------------------------------------------ tree interface ----
-template <int L> GBS_HD fxn<L> fms(const fxn<L>& x, const fxn<L>& a, const fxn<L>& b) { return x - a * b; }
-template <int L> GBS_HD fxn<L> fpa(const fxn<L>& x, const fxn<L>& a, const fxn<L>& b) { return x + a * b; }
+template <int L, int F> GBS_HD fxn<L, F> fms(const fxn<L, F>& x, const fxn<L, F>& a, const fxn<L, F>& b) {
+  return x - a * b;
+}
+template <int L, int F> GBS_HD fxn<L, F> fpa(const fxn<L, F>& x, const fxn<L, F>& a, const fxn<L, F>& b) {
+  return x + a * b;
+}
 template <> GBS_HD fx scale_<fx, fx>(const fx& x, const fx& s) { return x * s; }
 template <> GBS_HD fxw scale_<fxw, fxw>(const fxw& x, const fxw& s) { return x * s; }
 template <> GBS_HD fx conv_entry<fx>(const double& x) { return from_double<fx>(x); }
 template <> GBS_HD fxw conv_entry<fxw>(const double& x) { return from_double<fxw>(x); }
+template <> struct scale_of<fx> { typedef fxs type; };
+template <> struct scale_of<fxw> { typedef fxws type; };
 
 // A pivot determinant the fixed-point tree can use: in [2^-20, 2^12), where
 // its inverse square root keeps ~150 bits (the resolution is absolute, so the
-// relative error of 1/sqrt(x) grows like 2^-(32 (L-2)) x).
-template <int L>
-GBS_HD bool fx_det_in_range(const fxn<L>& d) {
-  return d.w[L - 1] == 0u && d.w[L - 2] < (1u << 12) && (d.w[L - 2] != 0u || d.w[L - 3] >= (1u << 12));
+// relative error of 1/sqrt(x) grows like 2^-(32 F) x).
+template <int L, int F>
+GBS_HD bool fx_det_in_range(const fxn<L, F>& d) {
+  bool high_zero = true;
+#pragma unroll
+  for (int k = F + 1; k < L; ++k) high_zero &= d.w[k] == 0u;
+  return high_zero && d.w[F] < (1u << 12) && (d.w[F] != 0u || d.w[F - 1] >= (1u << 12));
 }
-template <int L> GBS_HD bool not_positive(const fxn<L>& d) { return !fx_det_in_range(d); }
-template <int L> GBS_HD bool is_pos(const fxn<L>& d) { return fx_det_in_range(d); }
+template <int L, int F> GBS_HD bool not_positive(const fxn<L, F>& d) { return !fx_det_in_range(d); }
+template <int L, int F> GBS_HD bool is_pos(const fxn<L, F>& d) { return fx_det_in_range(d); }
 template <> constexpr int bad_status<fx>() { return kStatusRange; }
 template <> constexpr int bad_status<fxw>() { return kStatusRange; }
 
-// 1/sqrt(x) for x in [2^-20, 2^12): FP64 seed from the top limbs below the
-// sign limb, then Newton steps y <- y + y (1 - x y^2) / 2 (53 -> 106 -> 212 bits).
-template <int L>
-__device__ __forceinline__ fxn<L> rsqrt_(const fxn<L>& x) {
-  const double xd = fma((double)x.w[L - 3], 0x1p-32, (double)x.w[L - 2]) + (double)x.w[L - 4] * 0x1p-64;
-  fxn<L> y = fx_from_double<L>(rsqrt(xd));
-  fxn<L> one;
+// 1/sqrt(x) for x in [2^-20, 2^12): FP64 seed from the integer limb and the two
+// fraction limbs below it, then Newton steps y <- y + y (1 - x y^2) / 2
+// (53 -> 106 -> 212 bits).
+template <int L, int F>
+__device__ __forceinline__ fxn<L, F> rsqrt_(const fxn<L, F>& x) {
+  const double xd = fma((double)x.w[F - 1], 0x1p-32, (double)x.w[F]) + (double)x.w[F - 2] * 0x1p-64;
+  fxn<L, F> y = fx_from_double<L, F>(rsqrt(xd));
+  fxn<L, F> one;
 #pragma unroll
-  for (int k = 0; k < L; ++k) one.w[k] = k == L - 2 ? 1u : 0u;
+  for (int k = 0; k < L; ++k) one.w[k] = k == F ? 1u : 0u;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
-    const fxn<L> e = one - x * (y * y);
+    const fxn<L, F> e = one - x * (y * y);
     y = y + fx_half(y * e);
   }
   return y;
 }
 
 // ------------------------------------------------------ sums and reduction --
-template <int L> struct acc_traits<fxn<L>> { typedef fxn<L> Acc; typedef fxn<L> Red; };
-template <int L> GBS_HD void acc_add(fxn<L>& a, const fxn<L>& x) { a = a + x; }
-template <int L> GBS_HD void acc_sub(fxn<L>& a, const fxn<L>& x) { a = a - x; }
-template <int L> GBS_HD void acc_fpa(fxn<L>& acc, const fxn<L>& a, const fxn<L>& b) { acc = acc + a * b; }
-template <int L> GBS_HD fxn<L> red_diff(const fxn<L>& a, const fxn<L>& b, fxn<L>*) { return a - b; }
-template <int L> GBS_HD fxn<L> to_red(const fxn<L>& a, fxn<L>*) { return a; }
-template <int L> GBS_HD fxn<L> red_add(const fxn<L>& a, const fxn<L>& b) { return a + b; }
-template <int L> GBS_HD fxn<L> red_neg(const fxn<L>& a) { return -a; }
-template <> GBS_HD fx red_zero<fx>() { return from_double<fx>(0.0); }
-template <> GBS_HD fxw red_zero<fxw>() { return from_double<fxw>(0.0); }
+template <> struct acc_traits<fx> { typedef fxs Acc; typedef fxs Red; };
+template <> struct acc_traits<fxw> { typedef fxws Acc; typedef fxws Red; };
+template <int L, int F> GBS_HD void acc_add(fxn<L, F>& a, const fxn<L, F>& x) { a = a + x; }
+template <int L, int F> GBS_HD void acc_sub(fxn<L, F>& a, const fxn<L, F>& x) { a = a - x; }
+template <int L, int F>
+GBS_HD void acc_fpa(fxn<L + 1, F>& acc, const fxn<L + 1, F>& s, const fxn<L, F>& g) { acc = acc + s * g; }
+template <int L, int F> GBS_HD fxn<L, F> red_diff(const fxn<L, F>& a, const fxn<L, F>& b, fxn<L, F>*) { return a - b; }
+template <int L, int F> GBS_HD fxn<L, F> to_red(const fxn<L, F>& a, fxn<L, F>*) { return a; }
+template <int L, int F> GBS_HD fxn<L, F> red_add(const fxn<L, F>& a, const fxn<L, F>& b) { return a + b; }
+template <int L, int F> GBS_HD fxn<L, F> red_neg(const fxn<L, F>& a) { return -a; }
+template <> GBS_HD fxs red_zero<fxs>() { return from_double<fxs>(0.0); }
+template <> GBS_HD fxws red_zero<fxws>() { return from_double<fxws>(0.0); }
 // Three doubles whose sum is the value to ~2^-159 relative (each the nearest
 // double of what the previous ones left over; the differences are exact).
-template <int L>
-GBS_HD void red_store(const fxn<L>& a, double* o) {
+template <int L, int F>
+GBS_HD void red_store(const fxn<L, F>& a, double* o) {
   const double x0 = to_double(a);
-  const fxn<L> r1 = a - fx_from_double<L>(x0);
+  const fxn<L, F> r1 = a - fx_from_double<L, F>(x0);
   const double x1 = to_double(r1);
-  const fxn<L> r2 = r1 - fx_from_double<L>(x1);
+  const fxn<L, F> r2 = r1 - fx_from_double<L, F>(x1);
   o[0] = x0;
   o[1] = x1;
   o[2] = to_double(r2);
 }
-template <int L>
-__device__ __forceinline__ fxn<L> shfl_down(const fxn<L>& v, int off) {
-  fxn<L> r;
+template <int L, int F>
+__device__ __forceinline__ fxn<L, F> shfl_down(const fxn<L, F>& v, int off) {
+  fxn<L, F> r;
 #pragma unroll
   for (int k = 0; k < L; ++k) r.w[k] = __shfl_down_sync(0xffffffffu, v.w[k], off);
   return r;

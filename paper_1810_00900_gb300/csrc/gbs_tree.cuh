@@ -57,6 +57,10 @@ GBS_HD cplx<dd> scale_<cplx<dd>, dd>(const cplx<dd>& x, const dd& s) { return {x
 template <>
 GBS_HD cplx<td> scale_<cplx<td>, td>(const cplx<td>& x, const td& s) { return {x.re * s, x.im * s}; }
 
+// Type of the running product s of pivot factors: the entry scalar type,
+// except for the fixed-point entries, whose s needs a wider integer part.
+template <class E> struct scale_of { typedef typename real_of<E>::type type; };
+
 // ------------------------------------------------ accumulation types -----
 // Per-thread accumulators (Acc) and cross-thread reduction values (Red).
 template <class T> struct acc_traits;
@@ -151,10 +155,11 @@ GBS_HD bool is_pos(const td& x) { return x.x0 > 0.0; }
 // Children: 2*count nodes with q-1 modes; child 2i excludes the first mode of
 // node i, child 2i+1 includes it.
 template <class E>
-__global__ void tree_level_kernel(const E* __restrict__ par, const typename real_of<E>::type* __restrict__ spar,
+__global__ void tree_level_kernel(const E* __restrict__ par, const typename scale_of<E>::type* __restrict__ spar,
                                   long long count, int q, E* __restrict__ chi,
-                                  typename real_of<E>::type* __restrict__ schi, int* __restrict__ status) {
+                                  typename scale_of<E>::type* __restrict__ schi, int* __restrict__ status) {
   typedef typename real_of<E>::type T;
+  typedef typename scale_of<E>::type S;
   const int rows = 2 * q - 2;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= count * rows) return;
@@ -192,7 +197,7 @@ __global__ void tree_level_kernel(const E* __restrict__ par, const typename real
     chi[(long long)tri(a, a) * c2 + 2 * node + 1] = v;
   }
   if (a == 0) {
-    const T s = spar[node];
+    const S s = spar[node];
     schi[2 * node] = s;
     schi[2 * node + 1] = s * g;
   }
@@ -206,7 +211,8 @@ template <class E, int Q, int D, int OFF, bool NEG>
 struct Dfs {
   typedef typename real_of<E>::type T;
   typedef typename acc_traits<T>::Acc Acc;
-  static __device__ __forceinline__ void run(const E (&c)[sym(D)], const T& s, Sums<Acc>& acc, bool& bad) {
+  typedef typename scale_of<E>::type S;
+  static __device__ __forceinline__ void run(const E (&c)[sym(D)], const S& s, Sums<Acc>& acc, bool& bad) {
     const T p00 = re_of(c[tri(OFF, OFF)]);
     const T p11 = re_of(c[tri(OFF + 1, OFF + 1)]);
     const E p10 = c[tri(OFF + 1, OFF)];
@@ -253,7 +259,7 @@ GBS_HD dd red_diff(const dd& a, const dd& b, dd*) { return a - b; }
 GBS_HD td red_diff(const td& a, const td& b, td*) { return a - b; }
 
 template <class E, int Q, class Red>
-__device__ __forceinline__ bool subtree_sums(const E (&c)[sym(2 * Q)], const typename real_of<E>::type& s, Red& inc,
+__device__ __forceinline__ bool subtree_sums(const E (&c)[sym(2 * Q)], const typename scale_of<E>::type& s, Red& inc,
                                              Red& exc, double& asum) {
   typedef typename acc_traits<typename real_of<E>::type>::Acc Acc;
   Sums<Acc> a = sums_zero<Acc>();
@@ -290,7 +296,7 @@ __device__ __forceinline__ void block_reduce_store(Red inc, Red exc, double asum
 // One thread per node with Q undecided modes; depth = n - Q levels above.
 template <class E, int Q>
 __global__ void __launch_bounds__(128) tree_leaf_kernel(const E* __restrict__ nodes,
-                                                        const typename real_of<E>::type* __restrict__ snode,
+                                                        const typename scale_of<E>::type* __restrict__ snode,
                                                         long long count, int depth,
                                                         Partial<typename acc_traits<typename real_of<E>::type>::Red>* partials,
                                                         int* __restrict__ status) {
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(128) tree_leaf_kernel(const E* __restrict__ no
     E c[sym(2 * Q)];
 #pragma unroll
     for (int e = 0; e < sym(2 * Q); ++e) c[e] = nodes[(long long)e * count + node];
-    const T s = snode[node];
+    const typename scale_of<E>::type s = snode[node];
     if (!subtree_sums<E, Q>(c, s, inc, exc, asum)) atomicExch(status, (int)kStatusNotPD);
     // sign of the node: (-1)^(exclusions above) = (-1)^(depth - popcount(node))
     if ((depth - __popcll((unsigned long long)node)) & 1) { inc = red_neg(inc); exc = red_neg(exc); }

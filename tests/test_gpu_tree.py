@@ -154,7 +154,12 @@ def test_fixed_point_refusals(ctx):
         gbs.subset_sum(ctx, G, "real", "fx")
     assert e.value.status == 4
     G = np.eye(10)
-    G[8, 8] = G[9, 9] = 100.0  # pivot determinant 1e4 >= 2^12: reported by the device
+    G[8, 8] = G[9, 9] = 100.0  # eigenvalue above the fixed-point range: refused on the host
+    with pytest.raises(gbs.GbsError) as e:
+        gbs.subset_sum(ctx, G, "real", "fx")
+    assert e.value.status == 4
+    G = np.eye(10)
+    G[8, 8] = G[9, 9] = 64.0  # admitted, but its pivot determinant 4096 = 2^12: reported by the device
     with pytest.raises(gbs.GbsError) as e:
         gbs.subset_sum(ctx, G, "real", "fx")
     assert e.value.status == 4
