@@ -266,11 +266,9 @@ __device__ __forceinline__ fxn<L, F> rsqrt_(const fxn<L, F>& x) {
 template <> struct acc_traits<fx> { typedef fxs Acc; typedef fxs Red; };
 template <> struct acc_traits<fxw> { typedef fxws Acc; typedef fxws Red; };
 template <int L, int F> GBS_HD void acc_add(fxn<L, F>& a, const fxn<L, F>& x) { a = a + x; }
-template <int L, int F> GBS_HD void acc_sub(fxn<L, F>& a, const fxn<L, F>& x) { a = a - x; }
 template <int L, int F>
 GBS_HD void acc_fpa(fxn<L + 1, F>& acc, const fxn<L + 1, F>& s, const fxn<L, F>& g) { acc = acc + s * g; }
 template <int L, int F> GBS_HD fxn<L, F> red_diff(const fxn<L, F>& a, const fxn<L, F>& b, fxn<L, F>*) { return a - b; }
-template <int L, int F> GBS_HD fxn<L, F> to_red(const fxn<L, F>& a, fxn<L, F>*) { return a; }
 template <int L, int F> GBS_HD fxn<L, F> red_add(const fxn<L, F>& a, const fxn<L, F>& b) { return a + b; }
 template <int L, int F> GBS_HD fxn<L, F> red_neg(const fxn<L, F>& a) { return -a; }
 template <> GBS_HD fxs red_zero<fxs>() { return from_double<fxs>(0.0); }

@@ -45,15 +45,24 @@ __global__ void state_params_kernel(const double* __restrict__ r, double eta, in
 
 // Fixed-order double-double sum of x[0..n) by one block.
 __global__ void sum_dd_kernel(const double* __restrict__ x, int n, double* __restrict__ out) {
+  // strided per-thread sums, then a fixed-order shuffle tree within each warp
+  // and across the (at most 32) warps: deterministic, and no serial loop
   dd acc = dd_make(0.0);
   for (int i = threadIdx.x; i < n; i += blockDim.x) acc = acc + x[i];
-  __shared__ dd sh[256];
-  sh[threadIdx.x] = acc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+    acc = acc + dd{__shfl_down_sync(0xffffffffu, acc.hi, off), __shfl_down_sync(0xffffffffu, acc.lo, off)};
+  __shared__ dd sh[32];
+  if (lane == 0) sh[warp] = acc;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    dd t = sh[0];
-    for (int i = 1; i < blockDim.x; ++i) t = t + sh[i];
-    out[0] = t.hi + t.lo;
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    dd t = lane < nw ? sh[lane] : dd_make(0.0);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+      t = t + dd{__shfl_down_sync(0xffffffffu, t.hi, off), __shfl_down_sync(0xffffffffu, t.lo, off)};
+    if (lane == 0) out[0] = t.hi + t.lo;
   }
 }
 

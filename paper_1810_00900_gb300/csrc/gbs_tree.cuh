@@ -73,10 +73,6 @@ GBS_HD void acc_add(double& a, double x) { a += x; }
 GBS_HD void acc_add(double& a, float x) { a += (double)x; }
 GBS_HD void acc_add(dd& a, const dd& x) { a = a + x; }
 GBS_HD void acc_add(td& a, const td& x) { a = a + x; }
-GBS_HD void acc_sub(double& a, double x) { a -= x; }
-GBS_HD void acc_sub(double& a, float x) { a -= (double)x; }
-GBS_HD void acc_sub(dd& a, const dd& x) { a = a - x; }
-GBS_HD void acc_sub(td& a, const td& x) { a = a - x; }
 
 // acc += a * b (the term s * g of an included leaf)
 GBS_HD void acc_fpa(double& acc, double a, double b) { acc = fma(a, b, acc); }
@@ -105,9 +101,6 @@ GBS_HD bool not_positive(float) { return false; }
 GBS_HD bool not_positive(const dd&) { return false; }
 GBS_HD bool not_positive(const td&) { return false; }
 
-GBS_HD dd to_red(double a, dd*) { return dd_make(a); }
-GBS_HD dd to_red(const dd& a, dd*) { return a; }
-GBS_HD td to_red(const td& a, td*) { return a; }
 GBS_HD dd red_add(const dd& a, const dd& b) { return a + b; }
 GBS_HD td red_add(const td& a, const td& b) { return a + b; }
 GBS_HD dd red_neg(const dd& a) { return -a; }

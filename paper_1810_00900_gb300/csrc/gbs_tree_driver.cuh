@@ -12,7 +12,6 @@ namespace gbs {
 template <class E> struct root_src { typedef double type; };
 template <class T> struct root_src<cplx<T>> { typedef cplx<double> type; };
 
-template <class T> GBS_HD T conv_from64(double x) { return from_double<T>(x); }
 template <class E> GBS_HD E conv_entry(const typename root_src<E>::type& x);
 template <> GBS_HD double conv_entry<double>(const double& x) { return x; }
 template <> GBS_HD float conv_entry<float>(const double& x) { return (float)x; }
@@ -22,13 +21,5 @@ template <> GBS_HD cplx<double> conv_entry<cplx<double>>(const cplx<double>& x) 
 template <> GBS_HD cplx<float> conv_entry<cplx<float>>(const cplx<double>& x) { return {(float)x.re, (float)x.im}; }
 template <> GBS_HD cplx<dd> conv_entry<cplx<dd>>(const cplx<double>& x) { return {dd_make(x.re), dd_make(x.im)}; }
 template <> GBS_HD cplx<td> conv_entry<cplx<td>>(const cplx<double>& x) { return {td_make(x.re), td_make(x.im)}; }
-
-template <class E>
-__global__ void tree_root_kernel(const typename root_src<E>::type* __restrict__ g, int nent, E* __restrict__ root,
-                                 typename real_of<E>::type* __restrict__ s) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nent) root[i] = conv_entry<E>(g[i]);
-  if (i == 0) s[0] = from_double<typename real_of<E>::type>(1.0);
-}
 
 }  // namespace gbs
