@@ -183,8 +183,8 @@ def sampler_block(ctx, gbs, gi, n_traj, ws, local):
     (the paper's forced-outcome benchmark); p0 is evaluated at all 800 steps of every trajectory."""
     stp, clicks = gi.chain_sampling_workload(800, 20, n_traj, seed=2)
     st = gbs.build_state(ctx, stp.U, stp.r, stp.eta)
-    ctx.autotune("fx", "real", 18)
-    ctx.autotune("fxw", "real", 18)
+    ctx.autotune("fx", "real", 20)
+    ctx.autotune("fxw", "real", 20)
     ctx.autotune("td", "real", 18)
     forced = np.array(clicks, dtype=np.int32)
     gbs.sample(ctx, st, 2, seed=2, N_post=20, forced_clicks=forced[:2])  # warm-up
