@@ -148,6 +148,21 @@ def allreduce_max(ws, x: float, local: int) -> float:
     return float(t.item())
 
 
+def other_accountings(n: int, step_s: float):
+    """Flops per step under the per-subset Cholesky accountings, as context for the Schur tree's
+    count: complex (2k)^3/3 multiply-adds per subset of k modes without prefix reuse, and with
+    the shared prefix reused (only the trailing rows per subset, 4 (k-1)^2), 8 real flops each;
+    'equivalent' = those flops over the measured step time."""
+    from math import comb
+    ek3 = sum(comb(n, k) * k ** 3 for k in range(n + 1))
+    ekm12 = sum(comb(n, k) * max(k - 1, 0) ** 2 for k in range(n + 1))
+    no_reuse = 8.0 * (8.0 / 3.0) * ek3
+    prefix = 8.0 * 4.0 * ekm12
+    return {"cholesky_no_reuse_flops": no_reuse, "cholesky_prefix_reuse_flops": prefix,
+            "equivalent_tflops_no_reuse": no_reuse / step_s / 1e12,
+            "equivalent_tflops_prefix_reuse": prefix / step_s / 1e12}
+
+
 def captured_traffic(args, tuning):
     """DRAM bytes (read + write) per launch of the dominant kernel from the ncu capture summarised in
     profiles/batch_subtree_kernel_fp64_real_n24.md, when this run launches that same kernel shape
@@ -226,6 +241,34 @@ def certified_block(ctx, gbs, st, modes, steps, stream):
             "fx_tuning": ctx.tuning("fx", "real")}
 
 
+def complex_basis_block(ctx, gbs, st, modes, steps, stream, peak):
+    """The same N = 24 FP64 Torontonian with the click block in the complex (a, a^+) basis, the form
+    the determinants are usually written in (Hermitian 48 x 48); equal determinants, 4x the flops."""
+    import torch
+    ctx.autotune("fp64", "complex", 22)
+    for _ in range(2):
+        gbs.torontonian(ctx, st, modes, "fp64", "complex")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    ctx.kernel_time()
+    ctx.enable_timing(True)
+    for i in range(steps):
+        ev[i][0].record(stream)
+        gbs.torontonian(ctx, st, modes, "fp64", "complex")
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.enable_timing(False)
+    leaf_ms, leaf_n = ctx.kernel_time()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    t = ctx.tuning("fp64", "complex")
+    Q = max(1, min(4 - t["q_drop"], 24))
+    q_root = min(24, Q + t["sub_e"])
+    leaf_flops = (2 ** (24 - q_root)) * tree_flops(q_root, True)
+    achieved = leaf_flops / (leaf_ms / max(leaf_n, 1) * 1e-3) / 1e12
+    return {"metric": "Tor subset-terms/s (FP64, N=24, complex basis)", "value": 2.0 ** 24 / (ms * 1e-3),
+            "ms_per_evaluation": ms, "tuning": t, "flops_per_term": tree_flops(24, True) / 2.0 ** 24,
+            "dominant_kernel_tflops": achieved, "frac_of_fp64_peak": achieved / peak}
+
+
 def walltime_block(ctx, gbs, gi, ms):
     """One worst-case sample per click count m at the paper's Table II sizes (l modes,
     8 dB, all m clicks first), AUTO precision; the paper's Titan walltimes beside it as
@@ -270,6 +313,14 @@ def batched_block(ctx, gbs, gi, n_req, n_err):
     for st, pat in zip(states, pats):
         gbs.torontonian(ctx, st, pat, "fp64", "real")
     t_single = time.perf_counter() - t0
+    # the same batch certified to 1e-10 relative (AUTO: FP64, then fixed point, then triple-double)
+    t0 = time.perf_counter()
+    cert = gbs.torontonian_batch(ctx, states, pats, "auto", "real", check=False)
+    t_cert = time.perf_counter() - t0
+    prec_counts = {}
+    for c in cert:
+        prec_counts[c.prec] = prec_counts.get(c.prec, 0) + 1
+    worst_bound = max(c.err_bound / abs(c.p) for c in cert if c.p)
     # FP32 error study: relative error of FP32 and FP64 terms against the certified (AUTO) value
     idx = list(range(0, n_req, max(1, n_req // n_err)))[:n_err]
     sub_s, sub_p = [states[i] for i in idx], [pats[i] for i in idx]
@@ -290,6 +341,8 @@ def batched_block(ctx, gbs, gi, n_req, n_err):
             "batch_seconds": t_batch, "batch_requests_per_s": n_req / t_batch, "batch_terms_per_s": terms / t_batch,
             "one_at_a_time_seconds": t_single, "one_at_a_time_requests_per_s": n_req / t_single,
             "speedup_vs_one_at_a_time": t_single / t_batch, "batch_gpu_launches": launches,
+            "certified": {"seconds": t_cert, "requests_per_s": n_req / t_cert, "precisions": prec_counts,
+                          "max_rel_err_bound": worst_bound},
             "input_seconds": t_inputs, "fp32_error_study": err,
             "workload": "the first %d of 4096 requests: N~U{8..22}, M~U{100,200,400}, r~U[0.4,1.0], "
                         "eta~U[0.25,1.0], Haar seeded per request" % n_req}
@@ -573,6 +626,7 @@ def main():
             "flops_per_launch": leaf_flops, "leaf_ms_avg": leaf_avg_s * 1e3,
             "step_flops": total_flops,
             "step_tflops": total_flops * args.steps / (dev_ms * 1e-3) / 1e12,
+            "other_accountings": other_accountings(args.N, dev_ms * 1e-3 / args.steps),
         },
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -581,6 +635,7 @@ def main():
     }
     if args.prec == "fp64" and args.N == 24:
         line["certified"] = certified_block(ctx, gbs, st, modes, max(3, args.steps // 2), stream)
+        line["complex_basis"] = complex_basis_block(ctx, gbs, st, modes, max(3, args.steps // 2), stream, peak)
     if args.sampler_traj > 0:
         line["sampler"] = sampler_block(ctx, gbs, gi, args.sampler_traj, ws, local)
     if args.batched_req > 0:

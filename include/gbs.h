@@ -164,8 +164,9 @@ gbs_status gbs_sigma_inv_block(gbs_ctx* ctx, const gbs_state* st, const int* mod
  * triple-double).  prec: gbs_prec; basis: gbs_basis; out: caller-owned.
  * rel_tol (<= 0 means 1e-10) is the target relative error for GBS_PREC_AUTO.
  * Errors: GBS_EINVAL (N < 0 or N > 32, repeated or out-of-range modes),
- * GBS_ENOTPD, GBS_EPRECISION (AUTO could not meet rel_tol even in TD; *out then
- * holds the TD value), GBS_ENOMEM, GBS_ECUDA. */
+ * GBS_ENOTPD, GBS_EPRECISION (AUTO could not meet rel_tol even on its last rung --
+ * FXW where the state bounds the fixed-point tree, TD otherwise; *out then holds
+ * that value), GBS_ENOMEM, GBS_ECUDA. */
 gbs_status gbs_torontonian(gbs_ctx* ctx, const gbs_state* st, const int* modes, int N, int prec, int basis,
                            double rel_tol, gbs_prob* out);
 

@@ -227,7 +227,7 @@ __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
 
 // ---------------------------------------------------------------- level --
 template <class E>
-__global__ void batch_level_kernel(const LevelSeg* __restrict__ segs, int nseg, long long total,
+__global__ void __launch_bounds__(256, level_min_blocks<E>::value) batch_level_kernel(const LevelSeg* __restrict__ segs, int nseg, long long total,
                                    const E* __restrict__ in, const typename scale_of<E>::type* __restrict__ sin,
                                    E* __restrict__ out, typename scale_of<E>::type* __restrict__ sout,
                                    int* __restrict__ status) {

@@ -344,7 +344,12 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
     for (size_t i = 0; i < run.size(); ++i) {
       fill(&out[run[i]], res[i], pr, real, ld[i]);
       if (prec != GBS_PREC_AUTO) continue;
-      if (res[i].status == kStatusRange || (res[i].status == 0 && !(res[i].err <= tol * fabs(res[i].p_hi))))
+      const bool missed = res[i].status == 0 && !(res[i].err <= tol * fabs(res[i].p_hi));
+      // triple-double (u = 2^-152) cannot improve on a wide fixed-point result
+      // (2^-158): such a request stops here, uncertified
+      if (missed && pr == GBS_PREC_FXW)
+        uncertified = true;
+      else if (res[i].status == kStatusRange || missed)
         next.push_back(run[i]);
     }
     std::sort(next.begin(), next.end());

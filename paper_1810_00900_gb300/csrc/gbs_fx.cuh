@@ -242,6 +242,8 @@ GBS_HD bool fx_det_in_range(const fxn<L, F>& d) {
 template <int L, int F> GBS_HD bool not_positive(const fxn<L, F>& d) { return !fx_det_in_range(d); }
 template <int L, int F> GBS_HD bool is_pos(const fxn<L, F>& d) { return fx_det_in_range(d); }
 template <> constexpr int bad_status<fx>() { return kStatusRange; }
+template <> struct level_min_blocks<fx> { static const int value = 3; };
+template <> struct level_min_blocks<fxw> { static const int value = 3; };
 template <> constexpr int bad_status<fxw>() { return kStatusRange; }
 
 // 1/sqrt(x) for x in [2^-20, 2^12): FP64 seed from the integer limb and the two

@@ -337,10 +337,16 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
     }
     return (int)GBS_PREC_TD;
   };
+  // The next rung after a failed check; the wide fixed point is the last one
+  // where the state allows it (triple-double's bound is looser), so a half
+  // tree there is only redone as a full tree in the same precision.
   auto wider = [&](const Trajectory* t, int p, int n) {
     if (p == GBS_PREC_FP64 && fx_ok_sigma(t->st, n)) return (int)GBS_PREC_FX;
-    if (p == GBS_PREC_FX && fx_ok_sigma(t->st, n)) return (int)GBS_PREC_FXW;
+    if ((p == GBS_PREC_FX || p == GBS_PREC_FXW) && fx_ok_sigma(t->st, n)) return (int)GBS_PREC_FXW;
     return (int)GBS_PREC_TD;
+  };
+  auto last_rung = [&](const StepTree& q) {
+    return !q.half && (q.prec == GBS_PREC_TD || q.prec == GBS_PREC_FXW);
   };
   if ((e = stage_begin(ctx, act.size() * (2 * sizeof(GatherItem) + sizeof(DecideItem) + sizeof(CondItem) + 4 * 16384) +
                                 (1 << 16))))
@@ -420,8 +426,8 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
         const double p0 = exc > 0 ? inc / exc : INFINITY;
         dp = 4.0 * n * u * q.res.abs_sum * (1.0 + p0) / std::max(exc, 1e-300);
       }
-      if (!(dp < TOL) && (prec != GBS_PREC_AUTO || (q.prec == GBS_PREC_TD && !q.half))) stt.uncertified++;
-      if (prec == GBS_PREC_AUTO && !(dp < TOL) && !(q.prec == GBS_PREC_TD && !q.half)) {
+      if (!(dp < TOL) && (prec != GBS_PREC_AUTO || last_rung(q))) stt.uncertified++;
+      if (prec == GBS_PREC_AUTO && !(dp < TOL) && !last_rung(q)) {
         q.half = 0;
         q.n = q.tj->m + 1;
         q.prec = wider(q.tj, q.prec, q.n);

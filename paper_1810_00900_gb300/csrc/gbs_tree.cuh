@@ -61,6 +61,11 @@ GBS_HD cplx<td> scale_<cplx<td>, td>(const cplx<td>& x, const td& s) { return {x
 // except for the fixed-point entries, whose s needs a wider integer part.
 template <class E> struct scale_of { typedef typename real_of<E>::type type; };
 
+// Minimum resident CTAs per SM the compiler keeps registers for in the
+// breadth-first level kernel: the fixed-point levels wait on global loads with
+// too few warps otherwise.
+template <class E> struct level_min_blocks { static const int value = 1; };
+
 // ------------------------------------------------ accumulation types -----
 // Per-thread accumulators (Acc) and cross-thread reduction values (Red).
 template <class T> struct acc_traits;
