@@ -246,22 +246,89 @@ template <> struct level_min_blocks<fx> { static const int value = 3; };
 template <> struct level_min_blocks<fxw> { static const int value = 3; };
 template <> constexpr int bad_status<fxw>() { return kStatusRange; }
 
-// 1/sqrt(x) for x in [2^-20, 2^12): FP64 seed from the integer limb and the two
-// fraction limbs below it, then Newton steps y <- y + y (1 - x y^2) / 2
-// (53 -> 106 -> 212 bits).
+// a * b where b >= 0 has nonzero limbs only in [JLO, JHI] (and, when ILO/IHI
+// are given, a >= 0 only in [ILO, IHI]): the product of the general routine
+// restricted to those rows and columns (the carry of row i still lands in
+// column i + JHI + 1, which no earlier row reached), with the one correction a
+// negative a needs.
+template <int JLO, int JHI, int L, int F, int ILO = 0, int IHI = L - 1>
+__device__ __forceinline__ fxn<L, F> mul_short(const fxn<L, F>& a, const fxn<L, F>& b) {
+  constexpr int W = L, C0 = F;
+  uint32_t lo[W], hi[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) lo[k] = hi[k] = 0u;
+#pragma unroll
+  for (int i = ILO; i <= IHI; ++i) {
+    {
+      const int j0 = (C0 - i) > JLO ? (C0 - i) : JLO;
+      const int j1 = (C0 + W - 1 - i) < JHI ? (C0 + W - 1 - i) : JHI;
+      if (j0 <= j1) {
+        lo[i + j0 - C0] = mad_lo_cc(a.w[i], b.w[j0], lo[i + j0 - C0]);
+#pragma unroll
+        for (int j = j0 + 1; j <= j1; ++j) lo[i + j - C0] = madc_lo_cc(a.w[i], b.w[j], lo[i + j - C0]);
+        if (i + j1 + 1 - C0 < W) lo[i + j1 + 1 - C0] = addc(0u, 0u);
+      }
+    }
+    {
+      const int j0 = (C0 - 1 - i) > JLO ? (C0 - 1 - i) : JLO;
+      const int j1 = (C0 + W - 2 - i) < JHI ? (C0 + W - 2 - i) : JHI;
+      if (j0 <= j1) {
+        hi[i + j0 + 1 - C0] = mad_hi_cc(a.w[i], b.w[j0], hi[i + j0 + 1 - C0]);
+#pragma unroll
+        for (int j = j0 + 1; j <= j1; ++j) hi[i + j + 1 - C0] = madc_hi_cc(a.w[i], b.w[j], hi[i + j + 1 - C0]);
+        if (i + j1 + 2 - C0 < W) hi[i + j1 + 2 - C0] = addc(0u, 0u);
+      }
+    }
+  }
+  fxn<L, F> r;
+  r.w[0] = add_cc(lo[0], hi[0]);
+#pragma unroll
+  for (int k = 1; k < L - 1; ++k) r.w[k] = addc_cc(lo[k], hi[k]);
+  r.w[L - 1] = addc(lo[L - 1], hi[L - 1]);
+  constexpr int S = L - F;
+  const uint32_t ma = (uint32_t)((int32_t)a.w[L - 1] >> 31);
+  r.w[S] = sub_cc(r.w[S], b.w[0] & ma);
+#pragma unroll
+  for (int k = S + 1; k < L - 1; ++k) r.w[k] = subc_cc(r.w[k], b.w[k - S] & ma);
+  r.w[L - 1] = subc(r.w[L - 1], b.w[L - 1 - S] & ma);
+  return r;
+}
+
+// 1/sqrt(x) for x in [2^-20, 2^12).  Seed y0: FP64 inverse square root of the
+// value of the integer limb and the three fraction limbs below it (~53 bits);
+// y0 lies in (2^-6, 2^10], so its bits sit in limbs F-2 .. F.  Then, with
+// e = 1 - x y0^2 (|e| < 2^-50):
+//   160 fraction bits: one third-order step y0 (1 + e/2 + 3 e^2 / 8), whose
+//     remaining error 5 e^3 / 16 is below 2^-155 relative; e^2 comes from the
+//     double of e (the signed 64-bit integer of limbs F-2, F-3 plus limb F-4:
+//     e to 2^-128, so e^2 to 2^-175), and every product has y0 as its short
+//     factor (y0^2 is exact, so x y0^2 is truncated once);
+//   192 fraction bits: two Newton steps y <- y + y (1 - x y^2) / 2.
 template <int L, int F>
 __device__ __forceinline__ fxn<L, F> rsqrt_(const fxn<L, F>& x) {
-  const double xd = fma((double)x.w[F - 1], 0x1p-32, (double)x.w[F]) + (double)x.w[F - 2] * 0x1p-64;
-  fxn<L, F> y = fx_from_double<L, F>(rsqrt(xd));
+  const double xd = ((double)x.w[F] + (double)x.w[F - 1] * 0x1p-32) +
+                    ((double)x.w[F - 2] * 0x1p-64 + (double)x.w[F - 3] * 0x1p-96);
+  const fxn<L, F> y0 = fx_from_double<L, F>(rsqrt(xd));
   fxn<L, F> one;
 #pragma unroll
   for (int k = 0; k < L; ++k) one.w[k] = k == F ? 1u : 0u;
+  if constexpr (F == 5) {
+    // y0^2 has ~106 bits, all above 2^-117: exact in the window
+    const fxn<L, F> y2 = mul_short<F - 2, F, L, F, F - 2, F>(y0, y0);
+    const fxn<L, F> e = one - mul_short<F - 4, F>(x, y2);
+    const long long e96 = (long long)(((unsigned long long)e.w[F - 2] << 32) | e.w[F - 3]);
+    const double ed = fma((double)e.w[F - 4], 0x1p-128, (double)e96 * 0x1p-96);
+    const fxn<L, F> c = fx_half(e) + fx_from_double<L, F>(0.375 * ed * ed);
+    return y0 + mul_short<F - 2, F>(c, y0);
+  } else {
+    fxn<L, F> y = y0;
 #pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const fxn<L, F> e = one - x * (y * y);
-    y = y + fx_half(y * e);
+    for (int it = 0; it < 2; ++it) {
+      const fxn<L, F> e = one - x * (y * y);
+      y = y + fx_half(y * e);
+    }
+    return y;
   }
-  return y;
 }
 
 // ------------------------------------------------------ sums and reduction --
