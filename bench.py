@@ -198,9 +198,9 @@ def sampler_block(ctx, gbs, gi, n_traj, ws, local):
     (the paper's forced-outcome benchmark); p0 is evaluated at all 800 steps of every trajectory."""
     stp, clicks = gi.chain_sampling_workload(800, 20, n_traj, seed=2)
     st = gbs.build_state(ctx, stp.U, stp.r, stp.eta)
-    ctx.autotune("fx", "real", 20)
-    ctx.autotune("fxw", "real", 20)
-    ctx.autotune("td", "real", 18)
+    # the late steps batch 64 trees of ~13..21 modes: tune on such a batch
+    ctx.autotune("fx", "real", 21, n_trees=9)
+    ctx.autotune("fxw", "real", 21, n_trees=9)
     forced = np.array(clicks, dtype=np.int32)
     gbs.sample(ctx, st, 2, seed=2, N_post=20, forced_clicks=forced[:2])  # warm-up
     l0 = ctx.launch_count
@@ -214,8 +214,8 @@ def sampler_block(ctx, gbs, gi, n_traj, ws, local):
             "escalations": stats["escalations"], "uncertified_steps": stats["uncertified"],
             "gpu_launches": ctx.launch_count - l0,
             "trees_fp64_dd_td_fx_fxw": stats["trees"], "tree_seconds_fp64_dd_td_fx_fxw": stats["tree_seconds"],
-            "other_seconds": stats["cond_seconds"], "fx_tuning": ctx.tuning("fx", "real"), "fxw_tuning": ctx.tuning("fxw", "real"),
-            "td_tuning": ctx.tuning("td", "real"),
+            "other_seconds": stats["cond_seconds"], "fx_tuning": ctx.tuning("fx", "real"),
+            "fxw_tuning": ctx.tuning("fxw", "real"),
             "p0_range": [float(p0.min()), float(p0.max())], "status": status,
             "workload": "M=800 modes, r~U[0.3,0.9], Haar seed 2, eta=1; %d forced trajectories with 20 uniform "
                         "click positions; no-click probability at every one of the 800 steps" % n_traj}

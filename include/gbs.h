@@ -307,11 +307,13 @@ gbs_status gbs_server_stats_get(gbs_ctx* ctx, gbs_server_stats* out);
  *   mid_e          0..8: levels each first-kernel CTA goes on expanding in
  *                  shared memory after its prefix (replacing that many
  *                  breadth-first level launches; reduced to fit 200 KB).
- * gbs_autotune times candidate shapes on a synthetic n-mode tree (6 <= n <= 28)
+ * gbs_autotune times candidate shapes on a synthetic batch of n_trees (1..64)
+ * trees of n, n-1, ... modes (6 <= n <= 28; a workload of uneven trees tunes
+ * best on a batch that resembles it)
  * on the context stream and keeps the fastest for later calls; report (may be
  * NULL) receives the timings as a JSON array, truncated to report_len bytes.
  * The paper has no counterpart (its Titan runs used MPI + OpenMP, Sec. III). */
-gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, char* report, size_t report_len);
+gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, int n_trees, char* report, size_t report_len);
 gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub_e, int* d_top, int* grid_per_sm,
                           long long* level_threads, int* q_drop, int* mid_e);
 gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_top, int grid_per_sm,

@@ -108,8 +108,8 @@ def load() -> ctypes.CDLL:
                                            ctypes.c_double, ctypes.POINTER(gbs_prob)]),
         "gbs_torontonian_batch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), _ip, _ip, ctypes.c_int,
                                                  ctypes.c_int, ctypes.c_double, ctypes.POINTER(gbs_prob)]),
-        "gbs_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_char_p,
-                                        ctypes.c_size_t]),
+        "gbs_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_char_p, ctypes.c_size_t]),
         "gbs_get_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _ip, _ip, _ip,
                                           ctypes.POINTER(ctypes.c_longlong), _ip, _ip]),
         "gbs_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -197,11 +197,12 @@ class Context:
         self.check(self.L.gbs_measure_fp64_peak(self.h, ctypes.byref(g)))
         return g.value
 
-    def autotune(self, prec: str = "fp64", basis: str = "real", n: int = 22):
-        """Time candidate launch shapes on an n-mode tree and keep the fastest; returns the timings."""
+    def autotune(self, prec: str = "fp64", basis: str = "real", n: int = 22, n_trees: int = 1):
+        """Time candidate launch shapes on a batch of n_trees trees of n, n-1, ... modes and keep the
+        fastest; returns the timings."""
         import json
         buf = ctypes.create_string_buffer(1 << 16)
-        self.check(self.L.gbs_autotune(self.h, PREC[prec], BASIS[basis], int(n), buf, len(buf)))
+        self.check(self.L.gbs_autotune(self.h, PREC[prec], BASIS[basis], int(n), int(n_trees), buf, len(buf)))
         return json.loads(buf.value.decode() or "[]")
 
     def tuning(self, prec: str = "fp64", basis: str = "real") -> dict:

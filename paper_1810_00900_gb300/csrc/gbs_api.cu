@@ -24,15 +24,45 @@ gbs_status check_cuda(gbs_ctx* ctx, cudaError_t e, const char* what) {
   return set_error(ctx, GBS_ECUDA, buf);
 }
 
+// Give every cached block back to the driver (they leave in_use with it).
+void cache_release(gbs_ctx* ctx) {
+  std::lock_guard<std::mutex> g(ctx->cache_mu);
+  for (auto& kv : ctx->cache) {
+    cudaFree(kv.second);
+    ctx->in_use -= kv.first;
+  }
+  ctx->cache.clear();
+  ctx->cached = 0;
+}
+
 gbs_status dev_alloc(gbs_ctx* ctx, DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) / 256 * 256;
+  {
+    // reuse a cached block of at least the size and at most twice it
+    std::lock_guard<std::mutex> g(ctx->cache_mu);
+    auto it = ctx->cache.lower_bound(bytes);
+    if (it != ctx->cache.end() && it->first <= 2 * bytes) {
+      b.ptr = it->second;
+      b.bytes = it->first;
+      ctx->cached -= it->first;
+      ctx->cache.erase(it);
+      return GBS_OK;
+    }
+  }
+  if (ctx->budget && ctx->in_use.load() + bytes > ctx->budget) cache_release(ctx);
   if (ctx->budget && ctx->in_use.load() + bytes > ctx->budget)
     return set_error(ctx, GBS_ENOMEM, "device memory budget of the context exceeded");
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return set_error(ctx, GBS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    cache_release(ctx);  // the driver may have been short of memory held in the cache
+    e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(ctx, GBS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
   }
   b.ptr = p;
   b.bytes = bytes;
@@ -42,8 +72,14 @@ gbs_status dev_alloc(gbs_ctx* ctx, DevBuf& b, size_t bytes) {
 
 void dev_free(gbs_ctx* ctx, DevBuf& b) {
   if (b.ptr) {
-    cudaFree(b.ptr);
-    ctx->in_use -= b.bytes;
+    std::lock_guard<std::mutex> g(ctx->cache_mu);
+    if (ctx->cached + b.bytes <= ((size_t)1 << 30)) {  // keep up to 1 GiB of freed blocks
+      ctx->cache.emplace(b.bytes, b.ptr);
+      ctx->cached += b.bytes;
+    } else {
+      cudaFree(b.ptr);
+      ctx->in_use -= b.bytes;
+    }
   }
   b.ptr = nullptr;
   b.bytes = 0;
@@ -187,6 +223,7 @@ void gbs_ctx_destroy(gbs_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->lvl[0], &ctx->lvl[1], &ctx->sbuf[0], &ctx->sbuf[1], &ctx->partials,
                     &ctx->out,    &ctx->status, &ctx->hbuf,    &ctx->stage_dev, &ctx->aux_dev};
   for (DevBuf* b : bufs) dev_free(ctx, *b);
+  cache_release(ctx);
   if (ctx->leaf_timer.start) {
     cudaEventDestroy(ctx->leaf_timer.start);
     cudaEventDestroy(ctx->leaf_timer.stop);
@@ -202,6 +239,7 @@ gbs_status gbs_ctx_set_stream(gbs_ctx* ctx, void* stream) {
   std::lock_guard<std::mutex> g(ctx->mu);
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  cache_release(ctx);  // cached blocks were last used on the old stream
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   ctx->stream = (cudaStream_t)stream;
   ctx->own_stream = false;

@@ -368,8 +368,10 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
 
 using namespace gbs;
 
-extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, char* report, size_t report_len) {
-  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FXW || n < 6 || n > 28) return GBS_EINVAL;
+extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, int n_trees, char* report,
+                                   size_t report_len) {
+  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FXW || n < 6 || n > 28 || n_trees < 1 || n_trees > 64)
+    return GBS_EINVAL;
   if (prec >= GBS_PREC_FX && basis == GBS_BASIS_COMPLEX) return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
   cudaSetDevice(ctx->device);
@@ -387,9 +389,11 @@ extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, cha
       if (real) root[t] = v; else { root[2 * t] = v; root[2 * t + 1] = (a == b) ? 0.0 : 0.5 * v; }
     }
   gbs_status st;
-  const BatchTree tree{n, 0};
-  const double zero = 0.0;
-  ProbOut out;
+  // n_trees trees of n, n-1, ... modes (at least 6), all on leading blocks of the one root
+  std::vector<BatchTree> trees(n_trees);
+  for (int i = 0; i < n_trees; ++i) trees[i] = BatchTree{std::max(6, n - i), 0};
+  const std::vector<double> zeros(n_trees, 0.0);
+  std::vector<ProbOut> outs(n_trees);
   const BatchTune saved = ctx->tune[prec][real ? 1 : 0];
   BatchTune best = saved;
   double best_ms = 1e30;
@@ -421,7 +425,7 @@ extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, cha
             const void* d = nullptr;
             if ((st = stage(ctx, root.data(), root.size() * 8, &d))) goto done;
             cudaEventRecord(e0, ctx->stream);
-            if ((st = batch_eval(ctx, prec, real, 1, &tree, d, &zero, &out))) goto done;
+            if ((st = batch_eval(ctx, prec, real, n_trees, trees.data(), d, zeros.data(), outs.data()))) goto done;
             cudaEventRecord(e1, ctx->stream);
             cudaEventSynchronize(e1);
             float ms = 0.f;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -54,6 +55,13 @@ struct gbs_ctx {
   bool own_stream = false;
   std::string last_error;
   std::mutex mu;  // serialises calls that use the shared workspace
+  // Freed device blocks kept for reuse (stream-ordered: every use of a block is
+  // queued on the context's one stream, so a later allocation may take it at
+  // once); they stay counted in in_use, and are released when an allocation
+  // would exceed the budget, when the stream changes and at destruction.
+  std::mutex cache_mu;
+  std::multimap<size_t, void*> cache;
+  size_t cached = 0;
 
   // tree workspace (grown on demand)
   gbs::DevBuf lvl[2], sbuf[2], partials, out, status, hbuf;
@@ -104,6 +112,7 @@ gbs_status check_cuda(gbs_ctx* ctx, cudaError_t e, const char* what);
 gbs_status dev_alloc(gbs_ctx* ctx, DevBuf& b, size_t bytes);
 gbs_status dev_reserve(gbs_ctx* ctx, DevBuf& b, size_t bytes);  // grow-only
 void dev_free(gbs_ctx* ctx, DevBuf& b);
+void cache_release(gbs_ctx* ctx);  // return cached device blocks to the driver
 inline void count_launch(gbs_ctx* ctx, long long n = 1) { ctx->launches += n; }
 
 // Staging arena: stage_begin() makes room for `bytes` (synchronising first if it

@@ -304,7 +304,8 @@ gbs_status state_build(gbs_ctx* ctx, int M, const double* U, const double* r, do
   dev_free(ctx, tmp);
   if (V_out) {
     if ((e = ensure_V(ctx, st))) return fail(e);
-    if ((e = check_cuda(ctx, cudaMemcpy(V_out, st->V.ptr, 4 * MM * 16, cudaMemcpyDeviceToHost), "copy V")))
+    if ((e = check_cuda(ctx, cudaMemcpyAsync(V_out, st->V.ptr, 4 * MM * 16, cudaMemcpyDeviceToHost, s), "copy V")) ||
+        (e = check_cuda(ctx, cudaStreamSynchronize(s), "sync")))
       return fail(e);
   }
   *out = st;
