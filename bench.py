@@ -274,6 +274,9 @@ def walltime_block(ctx, gbs, gi, ms):
     8 dB, all m clicks first), AUTO precision; the paper's Titan walltimes beside it as
     context (hours on the quoted node counts, quad precision)."""
     paper = {10: (0.11, 1), 12: (0.68, 4), 14: (0.97, 32), 16: (1.98, 128), 18: (1.90, 1024), 20: (1.83, 8192)}
+    # one trajectory: each step is a single tree of up to m + 1 modes
+    ctx.autotune("fx", "real", max(ms) + 1)
+    ctx.autotune("fxw", "real", max(ms) + 1)
     rows = []
     for m in ms:
         stp, clicks = gi.walltime_workload(m)

@@ -201,7 +201,7 @@ class Context:
         """Time candidate launch shapes on a batch of n_trees trees of n, n-1, ... modes and keep the
         fastest; returns the timings."""
         import json
-        buf = ctypes.create_string_buffer(1 << 16)
+        buf = ctypes.create_string_buffer(1 << 18)
         self.check(self.L.gbs_autotune(self.h, PREC[prec], BASIS[basis], int(n), int(n_trees), buf, len(buf)))
         return json.loads(buf.value.decode() or "[]")
 

@@ -402,10 +402,11 @@ extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, int
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int subs[] = {0, 5, 6, 7};
-  const int tops[] = {6, 8, 10};
+  const int tops[] = {6, 8, 9, 10};
   const int grids[] = {0, 8};
   const long long lts[] = {1LL << 17, 1LL << 19};
-  for (int me = 0; me <= 5; me += 5)
+  const int mids[] = {0, 4, 5};
+  for (int me : mids)
   for (int qd = 0; qd < 2; ++qd)
   for (int se : subs)
     for (int dt : tops)
