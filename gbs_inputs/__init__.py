@@ -182,6 +182,13 @@ def walltime_workload(m: int, seed: int = 10):
     return st, np.arange(M - 1, M - 1 - m, -1, dtype=np.int64)
 
 
+def walltime_random_positions(m: int, count: int, seed: int = 10) -> np.ndarray:
+    """count sets of m click positions drawn uniformly from the WALLTIME_MODES[m] modes (the
+    paper's random-position runs beside the worst case)."""
+    M = WALLTIME_MODES[m]
+    return np.array([random_modes(M, m, seed + m, stream="clicks", start=i * m) for i in range(count)])
+
+
 def chain_sampling_workload(M: int = 800, n_clicks: int = 20, n_traj: int = 64, seed: int = 2):
     """M modes, r ~ U[0.3, 0.9] per mode, Haar unitary, no loss, plus n_traj forced
     click-position sets of n_clicks modes each (drawn uniformly, the paper's forced-outcome
