@@ -241,6 +241,36 @@ def certified_block(ctx, gbs, st, modes, steps, stream):
             "fx_tuning": ctx.tuning("fx", "real")}
 
 
+def paired_block(ctx, gbs, st, modes, steps, stream, cert, fp64_result):
+    """The same N = 24 Torontonian in FP64 with the last two tree levels summed cancellation-free:
+    device time per evaluation, its error bound, how much smaller its sum of group magnitudes is
+    than the plain sum of |terms| (and the effective cancellation ratio that leaves, against the
+    certified Torontonian), and the observed relative error against the certified (fixed-point)
+    value next to the plain FP64 one."""
+    import torch
+    ctx.autotune("fp64p", "real", 22)
+    for _ in range(2):
+        gbs.torontonian(ctx, st, modes, "fp64p", "real")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    res = []
+    for i in range(steps):
+        ev[i][0].record(stream)
+        res.append(gbs.torontonian(ctx, st, modes, "fp64p", "real"))
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    pr = res[-1]
+    ref = cert["p"]
+    return {"metric": "Tor subset-terms/s (FP64, last two levels cancellation-free, N=24)",
+            "value": 2.0 ** 24 / (ms * 1e-3), "ms_per_evaluation": ms, "tuning": ctx.tuning("fp64p", "real"),
+            "rel_err_bound": pr.err_bound / abs(pr.p),
+            "magnitude_sum_reduction": fp64_result.abs_sum / pr.abs_sum,
+            "kappa_groups": cert["kappa"] * pr.abs_sum / fp64_result.abs_sum,
+            "observed_rel_err_vs_certified": abs(pr.p - ref) / abs(ref),
+            "plain_fp64": {"rel_err_bound": fp64_result.err_bound / abs(fp64_result.p), "kappa": fp64_result.kappa,
+                           "observed_rel_err_vs_certified": abs(fp64_result.p - ref) / abs(ref)}}
+
+
 def complex_basis_block(ctx, gbs, st, modes, steps, stream, peak):
     """The same N = 24 FP64 Torontonian with the click block in the complex (a, a^+) basis, the form
     the determinants are usually written in (Hermitian 48 x 48); equal determinants, 4x the flops."""
@@ -308,7 +338,8 @@ def walltime_block(ctx, gbs, gi, ms):
 def batched_block(ctx, gbs, gi, n_req, n_err):
     """Uneven probability requests (N ~ U{8..22}, M ~ U{100, 200, 400}, r ~ U[0.4, 1.0],
     eta ~ U[0.25, 1.0], Haar unitary seeded per request) evaluated as one batch in FP64 and
-    one at a time; plus the FP32 error study on a subsample against certified values."""
+    one at a time; plus the FP32 / FP64 / paired-FP64 error study on a subsample against certified
+    values."""
     reqs = gi.batched_requests(4096)[:n_req]
     t0 = time.perf_counter()
     states = [gbs.build_state(ctx, gi.haar_unitary(q.M, q.seed), np.full(q.M, q.r), q.eta) for q in reqs]
@@ -338,14 +369,16 @@ def batched_block(ctx, gbs, gi, n_req, n_err):
     sub_s, sub_p = [states[i] for i in idx], [pats[i] for i in idx]
     ref = gbs.torontonian_batch(ctx, sub_s, sub_p, "auto", "real", check=False)
     f32 = gbs.torontonian_batch(ctx, sub_s, sub_p, "fp32", "real", check=False)
+    f64p = gbs.torontonian_batch(ctx, sub_s, sub_p, "fp64p", "real", check=False)
     by_n = {}
-    for i, r_, a, b in zip(idx, ref, f32, [batch[i] for i in idx]):
-        e32 = abs(a.p - r_.p) / abs(r_.p) if r_.p else float("inf")
-        e64 = abs(b.p - r_.p) / abs(r_.p) if r_.p else float("inf")
-        by_n.setdefault(reqs[i].N, []).append((e32, e64, r_.kappa))
+    for i, r_, a, b, c in zip(idx, ref, f32, [batch[i] for i in idx], f64p):
+        rel = (lambda x: abs(x.p - r_.p) / abs(r_.p) if r_.p else float("inf"))
+        by_n.setdefault(reqs[i].N, []).append((rel(a), rel(b), r_.kappa, rel(c), r_.kappa * c.abs_sum / r_.abs_sum))
     err = {int(n): {"fp32_median_rel_err": float(np.median([x[0] for x in v])),
                     "fp64_median_rel_err": float(np.median([x[1] for x in v])),
-                    "kappa_median": float(np.median([x[2] for x in v])), "count": len(v)}
+                    "fp64p_median_rel_err": float(np.median([x[3] for x in v])),
+                    "kappa_median": float(np.median([x[2] for x in v])),
+                    "kappa_groups_median": float(np.median([x[4] for x in v])), "count": len(v)}
            for n, v in sorted(by_n.items())}
     for st in states:
         st.free()
@@ -647,6 +680,8 @@ def main():
     }
     if args.prec == "fp64" and args.N == 24:
         line["certified"] = certified_block(ctx, gbs, st, modes, max(3, args.steps // 2), stream)
+        line["paired_fp64"] = paired_block(ctx, gbs, st, modes, max(3, args.steps // 2), stream, line["certified"],
+                                           results[-1])
         line["complex_basis"] = complex_basis_block(ctx, gbs, st, modes, max(3, args.steps // 2), stream, peak)
     if args.sampler_traj > 0:
         line["sampler"] = sampler_block(ctx, gbs, gi, args.sampler_traj, ws, local)

@@ -59,7 +59,8 @@ typedef int gbs_status;
 
 /* Per-term arithmetic of the subset enumeration. */
 typedef enum {
-  GBS_PREC_AUTO = 0,       /* cheapest of FP64 / FX / FXW / TD whose error estimate meets rel_tol */
+  GBS_PREC_AUTO = 0,       /* cheapest of FP64 / FP64P / FX / FXW / TD whose error estimate
+                              meets rel_tol (FP64P only where FP64 missed by <= 1e3) */
   GBS_PREC_FP64 = 1,       /* IEEE double */
   GBS_PREC_DD = 2,         /* double-double, ~106-bit significand */
   GBS_PREC_TD = 3,         /* triple-double, ~159-bit significand */
@@ -68,8 +69,16 @@ typedef enum {
                               160 fraction bits, range +-2^63; real basis only, and
                               only where the state bounds every value of the tree
                               (otherwise GBS_EPRECISION, or TD under AUTO) */
-  GBS_PREC_FXW = 6         /* wide fixed point, 256-bit integers: 192 fraction bits,
+  GBS_PREC_FXW = 6,        /* wide fixed point, 256-bit integers: 192 fraction bits,
                               same range and conditions as GBS_PREC_FX */
+  GBS_PREC_FP64P = 7       /* FP64 with the last two levels of the subset tree summed
+                              in a cancellation-free form: each group of four subsets
+                              that differ only in the last two modes adds one value
+                              whose factors carry small relative errors, so the
+                              error estimate follows the groups' magnitudes instead of
+                              the terms' (1e2..1e3 smaller on Haar states).  Real
+                              basis; Torontonians only (not the sampler's split sums).
+                              abs_sum / kappa then refer to the group magnitudes. */
 } gbs_prec;
 
 /* Basis of the matrices the enumeration factors.  Both give identical
@@ -328,7 +337,9 @@ gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_to
  * inc, exc, tor: caller-owned double[3] each (may be NULL), unevaluated sums.
  * prec must not be GBS_PREC_AUTO; GBS_PREC_FX / FXW need the real basis and a matrix
  * whose eigenvalues lie in [2^-8, 64] with (1 + 1/lambda_min)^n < 2^60
- * (checked on the host; otherwise GBS_EPRECISION).
+ * (checked on the host; otherwise GBS_EPRECISION).  GBS_PREC_FP64P (real basis)
+ * returns the whole sum in inc and zero in exc, and abs_sum is the sum of the
+ * group magnitudes.
  * Errors: GBS_EINVAL, GBS_ENOTPD, GBS_EPRECISION, GBS_ECUDA. */
 gbs_status gbs_subset_sum(gbs_ctx* ctx, int n, const double* G, int basis, int prec, double* inc, double* exc,
                           double* tor, double* abs_sum);

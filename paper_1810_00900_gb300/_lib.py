@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libgbs.so")
 HEADER = os.path.join(HERE, "..", "include", "gbs.h")
 
 OK, EINVAL, ENOMEM, ENOTPD, EPRECISION, EREJECT, ETIMEDOUT, ECUDA, PENDING, ENOTFOUND = range(10)
-PREC = {"auto": 0, "fp64": 1, "dd": 2, "td": 3, "fp32": 4, "fx": 5, "fxw": 6}
+PREC = {"auto": 0, "fp64": 1, "dd": 2, "td": 3, "fp32": 4, "fx": 5, "fxw": 6, "fp64p": 7}
 PREC_NAME = {v: k for k, v in PREC.items()}
 BASIS = {"auto": 0, "real": 1, "complex": 2}
 BASIS_NAME = {v: k for k, v in BASIS.items()}

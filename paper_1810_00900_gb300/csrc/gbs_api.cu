@@ -210,6 +210,8 @@ gbs_status gbs_ctx_create(gbs_ctx** out, int device, size_t hbm_budget_bytes) {
     ctx->tune[GBS_PREC_FX][b].d_top = 6;
     ctx->tune[GBS_PREC_FXW][b].sub_e = 6;
     ctx->tune[GBS_PREC_FXW][b].d_top = 6;
+    ctx->tune[GBS_PREC_FP64P][b].sub_e = 6;
+    ctx->tune[GBS_PREC_FP64P][b].d_top = 8;
   }
   *out = ctx;
   return GBS_OK;
@@ -340,7 +342,7 @@ gbs_status gbs_torontonian(gbs_ctx* ctx, const gbs_state* st, const int* modes, 
   cudaSetDevice(ctx->device);
   gbs_status e;
   if ((e = validate_modes(ctx, modes, N, st->M))) return e;
-  if (prec < GBS_PREC_AUTO || prec > GBS_PREC_FXW) return set_error(ctx, GBS_EINVAL, "bad precision");
+  if (prec < GBS_PREC_AUTO || prec > GBS_PREC_FP64P) return set_error(ctx, GBS_EINVAL, "bad precision");
   const int* mp[1] = {modes};
   const int Nv[1] = {N};
   return probs_batch(ctx, 1, &st, mp, Nv, prec, basis, rel_tol, out);
@@ -349,7 +351,7 @@ gbs_status gbs_torontonian(gbs_ctx* ctx, const gbs_state* st, const int* modes, 
 gbs_status gbs_subset_sum(gbs_ctx* ctx, int n, const double* G, int basis, int prec, double* inc, double* exc,
                           double* tor, double* abs_sum) {
   if (!ctx || !G || n < 1 || n > 32) return GBS_EINVAL;
-  if (prec < GBS_PREC_FP64 || prec > GBS_PREC_FXW) return GBS_EINVAL;
+  if (prec < GBS_PREC_FP64 || prec > GBS_PREC_FP64P) return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
   cudaSetDevice(ctx->device);
   const bool real = basis != GBS_BASIS_COMPLEX;

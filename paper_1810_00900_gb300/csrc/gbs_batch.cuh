@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(256, level_min_blocks<E>::value) batch_level_k
 }
 
 // ----------------------------------------------------------------- leaf --
-template <class E, int Q>
+template <class E, int Q, bool PAIR = false>
 __global__ void __launch_bounds__(128) batch_leaf_kernel(const LeafSeg* __restrict__ segs, int nseg,
                                                          long long total_blocks, const E* __restrict__ buf0,
                                                          const E* __restrict__ buf1,
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(128) batch_leaf_kernel(const LeafSeg* __restri
 #pragma unroll
       for (int e = 0; e < sym(2 * Q); ++e) c[e] = nodes[(long long)e * sg.count + node];
       const typename scale_of<E>::type s = (sg.buf ? s1 : s0)[sg.s_base + node];
-      if (!subtree_sums<E, Q>(c, s, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
+      if (!subtree_sums<E, Q, PAIR>(c, s, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
       if ((sg.depth - __popcll((unsigned long long)node)) & 1) {
         inc = red_neg(inc);
         exc = red_neg(exc);
@@ -327,7 +327,7 @@ struct SubSeg {
   int q_root, e_levels, depth_leaf, tree, buf, pad;
 };
 
-template <class E, int Q>
+template <class E, int Q, bool PAIR = false>
 __global__ void __launch_bounds__(128) batch_subtree_kernel(
     const SubSeg* __restrict__ segs, int nseg, long long total_blocks, const E* __restrict__ buf0,
     const E* __restrict__ buf1, const typename scale_of<E>::type* __restrict__ s0,
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
 #pragma unroll
       for (int e = 0; e < sym(2 * Q); ++e) c[e] = src[e * nodes + t];
       const S sv = ssrc[t];
-      if (!subtree_sums<E, Q>(c, sv, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
+      if (!subtree_sums<E, Q, PAIR>(c, sv, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
       const unsigned long long gnode = ((unsigned long long)root << sg.e_levels) | (unsigned long long)t;
       if ((sg.depth_leaf - __popcll(gnode)) & 1) {
         inc = red_neg(inc);

@@ -45,7 +45,7 @@ gbs_status stage(gbs_ctx* ctx, const void* data, size_t bytes, const void** dev)
 }
 
 const BatchTune& batch_tune_for(gbs_ctx* ctx, int prec, bool real) {
-  return ctx->tune[prec < 0 || prec > GBS_PREC_FXW ? 1 : prec][real ? 1 : 0];
+  return ctx->tune[prec < 0 || prec > GBS_PREC_FP64P ? 1 : prec][real ? 1 : 0];
 }
 
 // Every value of a tree over n modes of (Sigma^-1)_S fits the fixed-point
@@ -173,7 +173,8 @@ __global__ void batch_finish_kernel(const TreeOut* __restrict__ outs, const int*
 
 static double unit_roundoff_b(int prec) {
   switch (prec) {
-    case GBS_PREC_FP64: return ldexp(1.0, -53);
+    case GBS_PREC_FP64:
+    case GBS_PREC_FP64P: return ldexp(1.0, -53);
     case GBS_PREC_DD: return ldexp(1.0, -102);
     case GBS_PREC_TD: return ldexp(1.0, -152);
     case GBS_PREC_FP32_DIAG: return ldexp(1.0, -24);
@@ -199,6 +200,8 @@ static gbs_status batch_variant(gbs_ctx* ctx, int prec, bool real, int nt, const
                                   : set_error(ctx, GBS_EINVAL, "the fixed-point precision needs the real basis");
     case GBS_PREC_FXW: return real ? batch_fxw_real(ctx, nt, tr, roots, outs, status, tu)
                                    : set_error(ctx, GBS_EINVAL, "the fixed-point precision needs the real basis");
+    case GBS_PREC_FP64P: return real ? batch_fp64p_real(ctx, nt, tr, roots, outs, status, tu)
+                                     : set_error(ctx, GBS_EINVAL, "the paired FP64 precision needs the real basis");
   }
   return set_error(ctx, GBS_EINVAL, "unknown precision");
 }
@@ -313,16 +316,26 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
       todo.push_back(i);
     }
   }
-  // AUTO: FP64, then fixed point (160, then 192 fraction bits) where the state
-  // bounds the tree (real basis), then triple-double; a request moves on while
-  // its error estimate misses rel_tol or its fixed-point tree left the range.
-  const int ladder[4] = {GBS_PREC_FP64, GBS_PREC_FX, GBS_PREC_FXW, GBS_PREC_TD};
-  const int steps = prec == GBS_PREC_AUTO ? 4 : 1;
+  // AUTO: FP64; then FP64 with the last two levels cancellation-free (real
+  // basis) for the requests whose FP64 estimate missed rel_tol by at most
+  // kPairReach (the grouping's estimate is 1e1 to 1e3 below FP64's on the
+  // states it was measured on); then fixed point (160, then 192 fraction bits) where the
+  // state bounds the tree (real basis), then triple-double.  A request moves
+  // on while its error estimate misses rel_tol or its fixed-point tree left the
+  // range.
+  constexpr double kPairReach = 1e3;
+  const int ladder[5] = {GBS_PREC_FP64, GBS_PREC_FP64P, GBS_PREC_FX, GBS_PREC_FXW, GBS_PREC_TD};
+  const int steps = prec == GBS_PREC_AUTO ? 5 : 1;
   bool uncertified = false;
   for (int k = 0; k < steps && !todo.empty(); ++k) {
     const int pr = prec == GBS_PREC_AUTO ? ladder[k] : prec;
     std::vector<int> run, next;
     for (int i : todo) {
+      if (prec == GBS_PREC_AUTO && pr == GBS_PREC_FP64P &&
+          !(real && out[i].err_bound <= kPairReach * tol * fabs(out[i].p_hi))) {
+        next.push_back(i);
+        continue;
+      }
       if ((pr == GBS_PREC_FX || pr == GBS_PREC_FXW) && !(real && fx_ok_inverse(states[i], N[i]))) {
         if (prec == GBS_PREC_AUTO) {
           next.push_back(i);
@@ -370,7 +383,7 @@ using namespace gbs;
 
 extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, int n_trees, char* report,
                                    size_t report_len) {
-  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FXW || n < 6 || n > 28 || n_trees < 1 || n_trees > 64)
+  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP64P || n < 6 || n > 28 || n_trees < 1 || n_trees > 64)
     return GBS_EINVAL;
   if (prec >= GBS_PREC_FX && basis == GBS_BASIS_COMPLEX) return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
@@ -459,7 +472,7 @@ done:
 
 extern "C" gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub_e, int* d_top, int* grid_per_sm,
                                      long long* level_threads, int* q_drop, int* mid_e) {
-  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FXW) return GBS_EINVAL;
+  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP64P) return GBS_EINVAL;
   const BatchTune& t = ctx->tune[prec][basis != GBS_BASIS_COMPLEX ? 1 : 0];
   if (sub_e) *sub_e = t.sub_e;
   if (d_top) *d_top = t.d_top;
@@ -472,7 +485,7 @@ extern "C" gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub
 
 extern "C" gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_top, int grid_per_sm,
                                      long long level_threads, int q_drop, int mid_e) {
-  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FXW || sub_e < 0 || sub_e > 7 ||
+  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP64P || sub_e < 0 || sub_e > 7 ||
       (sub_e > 0 && sub_e < 5) || d_top < 0 ||
       d_top > 16 || grid_per_sm < 0 || level_threads < 1 || q_drop < 0 || q_drop > 2 || mid_e < 0 || mid_e > 8)
     return GBS_EINVAL;
@@ -491,7 +504,7 @@ extern "C" gbs_status gbs_torontonian_batch(gbs_ctx* ctx, int n_req, const gbs_s
                                             const int* modes, const int* N_per, int prec, int basis, double rel_tol,
                                             gbs_prob* out) {
   if (!ctx || n_req < 0 || (n_req > 0 && (!states || !N_per || !out))) return GBS_EINVAL;
-  if (prec < GBS_PREC_AUTO || prec > GBS_PREC_FXW) return GBS_EINVAL;
+  if (prec < GBS_PREC_AUTO || prec > GBS_PREC_FP64P) return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
   cudaSetDevice(ctx->device);
   std::vector<const int*> mp(n_req);

@@ -21,7 +21,9 @@ struct Blob {
 };
 
 
-template <class E, int QMAX>
+// PAIR: the last two levels of every tree as cancellation-free groups (FP64
+// real basis; the tree's inc output then carries the whole Torontonian).
+template <class E, int QMAX, bool PAIR = false>
 gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const void* roots_dev, TreeOut* outs_dev,
                      int* status_dev, const BatchTune& tune) {
   typedef typename real_of<E>::type T;
@@ -213,15 +215,15 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
     if constexpr (QQ <= QMAX) {                                                                                 \
       if (sub_e > 0) {                                                                                          \
         if ((st = check_cuda(ctx,                                                                               \
-                             cudaFuncSetAttribute(batch_subtree_kernel<E, QQ>,                                  \
+                             cudaFuncSetAttribute(batch_subtree_kernel<E, QQ, PAIR>,                                  \
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sub), \
                              "subtree smem")))                                                                  \
           return st;                                                                                            \
-        batch_subtree_kernel<E, QQ><<<(unsigned)grid, nthr, smem_sub, s>>>(                                    \
+        batch_subtree_kernel<E, QQ, PAIR><<<(unsigned)grid, nthr, smem_sub, s>>>(                                    \
             (const SubSeg*)(plan + o_leaf[qv]), ns, nb, buf[0], buf[1], sb[0], sb[1], capA, capB, pp,           \
             status_dev);                                                                                        \
       } else {                                                                                                  \
-        batch_leaf_kernel<E, QQ><<<(unsigned)grid, 128, 0, s>>>((const LeafSeg*)(plan + o_leaf[qv]), ns, nb,   \
+        batch_leaf_kernel<E, QQ, PAIR><<<(unsigned)grid, 128, 0, s>>>((const LeafSeg*)(plan + o_leaf[qv]), ns, nb,   \
                                                                 buf[0], buf[1], sb[0], sb[1], pp, status_dev);  \
       }                                                                                                         \
     }                                                                                                           \

@@ -81,8 +81,8 @@ struct gbs_ctx {
   int sm_count = 0;
 
   // batched-engine launch parameters per (precision, basis): [prec][real]
-  gbs::BatchTune tune[7][2];  // [gbs_prec][basis is real]
-  bool tuned[7][2] = {};
+  gbs::BatchTune tune[8][2];  // [gbs_prec][basis is real]
+  bool tuned[8][2] = {};
 
   // request loop (see gbs_server.cu)
   void* server = nullptr;
@@ -139,6 +139,7 @@ gbs_status batch_td_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*,
 gbs_status batch_td_cplx(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 gbs_status batch_fx_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 gbs_status batch_fxw_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
+gbs_status batch_fp64p_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 gbs_status batch_fp32_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 gbs_status batch_fp32_cplx(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 

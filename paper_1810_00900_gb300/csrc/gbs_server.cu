@@ -341,7 +341,7 @@ gbs_status validate(gbs_ctx* ctx, const gbs_request* r, std::vector<int>& modes)
   if (r->kind == GBS_REQ_PROB) {
     if (r->N < 0 || r->N > 32) return set_error(ctx, GBS_EINVAL, "request: N must be in [0, 32]");
     if (r->N > 0 && !r->modes) return set_error(ctx, GBS_EINVAL, "request: modes is NULL");
-    if (r->prec < GBS_PREC_AUTO || r->prec > GBS_PREC_FXW) return set_error(ctx, GBS_EINVAL, "request: prec");
+    if (r->prec < GBS_PREC_AUTO || r->prec > GBS_PREC_FP64P) return set_error(ctx, GBS_EINVAL, "request: prec");
     modes.assign(r->modes, r->modes + r->N);
     std::vector<int> s = modes;
     std::sort(s.begin(), s.end());

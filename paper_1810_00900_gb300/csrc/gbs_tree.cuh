@@ -31,6 +31,8 @@
 //   reduction           per-block partials in the accumulation type, then one
 //                       block sums them in a fixed order (bitwise deterministic).
 #pragma once
+#include <type_traits>
+
 #include "gbs_num.cuh"
 
 namespace gbs {
@@ -202,15 +204,95 @@ __global__ void tree_level_kernel(const E* __restrict__ par, const typename scal
 #undef PAR
 }
 
+// ------------------------------------ last two levels without cancellation --
+// The four leaves below a node with two undecided modes a, b (in that order)
+// carry g_a g_c, -g_a, -g_b, +1 times the node's s and sign, where g_x =
+// det(P_x)^(-1/2) for the pivot blocks P_a, P_b and P_c = P_b - D of b given a
+// (D = B P_a^-1 B^T, B the b-by-a block).  Their sum is rewritten as
+//   v = (g_a - 1)(g_c - 1) + (g_c - g_b)
+// with every factor evaluated to a small relative error:
+//   g - 1 from x = det(P) - 1 = (1 - p00)(1 - p11) - p01^2 - 1 formed from the
+//     deviations o = 1 - p, then one Newton step on (1 + h)^2 (1 + x) = 1
+//     from h = g - 1;
+//   g_c - g_b from delta = det(P_c) - det(P_b) = -tr(adj(P_b) D) + det D, then
+//     one Newton step on (g_b + y)^2 (det P_b + delta) = g_b^2 det P_b from
+//     y = g_c - g_b.
+// The alternating sum then adds one v per four subsets, and the terms that
+// cancelled inside each group never reach it.  The magnitude a group reports
+// for the error estimate covers both the rounding of its two parts and the
+// first-order effect of relative perturbations of its input entries:
+//   m = |(g_a-1)(g_c-1)| + |g_c-g_b| + |g_a-1| g_c + |g_c-1| g_a + |D00| + |D11|
+// (the pivot blocks enter v through the small factors g - 1, the coupling B
+// through D), so that sum s m / |Tor| replaces sum|t| / |Tor| in the estimate
+// (1e2 to 1e3 smaller on the 200-mode states).  Real basis, FP64 only.
+__device__ __forceinline__ double pair_hm1(double p00, double p11, double p01, double det, double g) {
+  const double o00 = 1.0 - p00, o11 = 1.0 - p11;
+  const double x = fma(-p01, p01, fma(o00, o11, -(o00 + o11)));
+  const double h = g - 1.0;
+  const double r = fma(h * (2.0 + h), det, x);  // (1 + h)^2 det - 1
+  return fma(-0.5 * g, r, h);
+}
+
+// Adds (-1)^NEG s v to acc.ip and s m to acc.ep.
+template <int D, int OFF, bool NEG>
+__device__ __forceinline__ void pair_group(const double (&c)[sym(D)], double s, Sums<double>& acc) {
+  const double a00 = c[tri(OFF, OFF)], a11 = c[tri(OFF + 1, OFF + 1)], a01 = c[tri(OFF + 1, OFF)];
+  const double b00 = c[tri(OFF + 2, OFF + 2)], b11 = c[tri(OFF + 3, OFF + 3)], b01 = c[tri(OFF + 3, OFF + 2)];
+  const double u00 = c[tri(OFF + 2, OFF)], u01 = c[tri(OFF + 2, OFF + 1)];
+  const double u10 = c[tri(OFF + 3, OFF)], u11 = c[tri(OFF + 3, OFF + 1)];
+  const double da = fma(a00, a11, -a01 * a01);
+  const double ga = rsqrt(da);
+  const double inv = ga * ga;
+  const double q00 = a00 * inv, q11 = a11 * inv, m = -a01 * inv;
+  // rows of B P_a^-1, then D = B P_a^-1 B^T
+  const double l0 = fma(u00, q11, u01 * m), l1 = fma(u01, q00, u00 * m);
+  const double k0 = fma(u10, q11, u11 * m), k1 = fma(u11, q00, u10 * m);
+  const double d00 = fma(l0, u00, l1 * u01);
+  const double d11 = fma(k0, u10, k1 * u11);
+  const double d01 = fma(k0, u00, k1 * u01);
+  const double c00 = b00 - d00, c11 = b11 - d11, c01 = b01 - d01;
+  const double db = fma(b00, b11, -b01 * b01);
+  const double dc = fma(c00, c11, -c01 * c01);
+  const double gb = rsqrt(db), gc = rsqrt(dc);
+  const double ha = pair_hm1(a00, a11, a01, da, ga);
+  const double hc = pair_hm1(c00, c11, c01, dc, gc);
+  const double delta = fma(d00, d11, -d01 * d01) - fma(b11, d00, fma(b00, d11, -2.0 * b01 * d01));
+  double y = gc - gb;
+  const double f = fma(gb * gb, delta, y * (2.0 * gb + y) * (db + delta));
+  y = fma(-0.5 * gc, f, y);
+  const double hh = ha * hc;
+  const double v = hh + y;
+  if (NEG) acc.ip = fma(-s, v, acc.ip); else acc.ip = fma(s, v, acc.ip);
+  const double m_in = fma(fabs(ha), gc, fabs(hc) * ga) + (fabs(d00) + fabs(d11));
+  acc.ep = fma(s, (fabs(hh) + fabs(y)) + m_in, acc.ep);
+}
+
+// A tree of one mode: Tor = g - 1 (magnitude |g - 1| + g: the pivot block
+// enters with the full g).
+template <int D, int OFF, bool NEG>
+__device__ __forceinline__ void pair_single(const double (&c)[sym(D)], double s, Sums<double>& acc) {
+  const double p00 = c[tri(OFF, OFF)], p11 = c[tri(OFF + 1, OFF + 1)], p01 = c[tri(OFF + 1, OFF)];
+  const double det = fma(p00, p11, -p01 * p01);
+  const double g = rsqrt(det);
+  const double h = pair_hm1(p00, p11, p01, det, g);
+  if (NEG) acc.ip = fma(-s, h, acc.ip); else acc.ip = fma(s, h, acc.ip);
+  acc.ep = fma(s, fabs(h) + g, acc.ep);
+}
+
 // ----------------------------------------------- register depth-first ----
 // Node with Q undecided modes whose matrix is the view c[tri(OFF + i, OFF + j)]
-// of an array of dimension D; NEG = odd number of exclusions above it.
-template <class E, int Q, int D, int OFF, bool NEG>
+// of an array of dimension D; NEG = odd number of exclusions above it.  PAIR:
+// the last two levels as cancellation-free groups (above; E = double only).
+template <class E, int Q, int D, int OFF, bool NEG, bool PAIR = false>
 struct Dfs {
   typedef typename real_of<E>::type T;
   typedef typename acc_traits<T>::Acc Acc;
   typedef typename scale_of<E>::type S;
   static __device__ __forceinline__ void run(const E (&c)[sym(D)], const S& s, Sums<Acc>& acc, bool& bad) {
+    if constexpr (PAIR && Q <= 2) {
+      static_assert(std::is_same<E, double>::value, "the paired last levels are FP64 real-basis only");
+      if constexpr (Q == 2) pair_group<D, OFF, NEG>(c, s, acc); else pair_single<D, OFF, NEG>(c, s, acc);
+    } else {
     const T p00 = re_of(c[tri(OFF, OFF)]);
     const T p11 = re_of(c[tri(OFF + 1, OFF + 1)]);
     const E p10 = c[tri(OFF + 1, OFF)];
@@ -239,8 +321,9 @@ struct Dfs {
         E v = fms_conj_re(c[tri(OFF + 2 + a, OFF + 2 + a)], L0, u0);
         cn[tri(a, a)] = fms_conj_re(v, L1, u1);
       }
-      Dfs<E, Q - 1, DN, 0, NEG>::run(cn, s * g, acc, bad);
-      Dfs<E, Q - 1, D, OFF + 2, !NEG>::run(c, s, acc, bad);
+      Dfs<E, Q - 1, DN, 0, NEG, PAIR>::run(cn, s * g, acc, bad);
+      Dfs<E, Q - 1, D, OFF + 2, !NEG, PAIR>::run(c, s, acc, bad);
+    }
     }
   }
 };
@@ -256,17 +339,26 @@ GBS_HD dd red_diff(double a, double b, dd*) {
 GBS_HD dd red_diff(const dd& a, const dd& b, dd*) { return a - b; }
 GBS_HD td red_diff(const td& a, const td& b, td*) { return a - b; }
 
-template <class E, int Q, class Red>
+// PAIR: inc receives the node's Torontonian (every group's v), exc zero, and
+// asum the sum of the group magnitudes.
+template <class E, int Q, bool PAIR = false, class Red>
 __device__ __forceinline__ bool subtree_sums(const E (&c)[sym(2 * Q)], const typename scale_of<E>::type& s, Red& inc,
                                              Red& exc, double& asum) {
   typedef typename acc_traits<typename real_of<E>::type>::Acc Acc;
   Sums<Acc> a = sums_zero<Acc>();
   bool bad = false;
-  Dfs<E, Q, 2 * Q, 0, false>::run(c, s, a, bad);
-  inc = red_diff(a.ip, a.in, (Red*)nullptr);
-  exc = red_diff(a.ep, a.en, (Red*)nullptr);
-  asum = to_double(a.ip) + to_double(a.in) + (to_double(a.ep) + to_double(a.en));
-  return !bad && isfinite(asum);
+  Dfs<E, Q, 2 * Q, 0, false, PAIR>::run(c, s, a, bad);
+  if constexpr (PAIR) {
+    inc = red_diff(a.ip, a.in, (Red*)nullptr);
+    exc = red_zero<Red>();
+    asum = to_double(a.ep);
+    return isfinite(asum) && isfinite(to_double(a.ip));
+  } else {
+    inc = red_diff(a.ip, a.in, (Red*)nullptr);
+    exc = red_diff(a.ep, a.en, (Red*)nullptr);
+    asum = to_double(a.ip) + to_double(a.in) + (to_double(a.ep) + to_double(a.en));
+    return !bad && isfinite(asum);
+  }
 }
 
 template <class Red>
