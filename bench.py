@@ -199,6 +199,7 @@ def sampler_block(ctx, gbs, gi, n_traj, ws, local):
     stp, clicks = gi.chain_sampling_workload(800, 20, n_traj, seed=2)
     st = gbs.build_state(ctx, stp.U, stp.r, stp.eta)
     # the late steps batch 64 trees of ~13..21 modes: tune on such a batch
+    ctx.autotune("fxn", "real", 21, n_trees=9)
     ctx.autotune("fx", "real", 21, n_trees=9)
     ctx.autotune("fxw", "real", 21, n_trees=9)
     forced = np.array(clicks, dtype=np.int32)
@@ -213,9 +214,9 @@ def sampler_block(ctx, gbs, gi, n_traj, ws, local):
             "seconds": dt, "trajectories": n_traj, "steps_evaluated": stats["steps"],
             "escalations": stats["escalations"], "uncertified_steps": stats["uncertified"],
             "gpu_launches": ctx.launch_count - l0,
-            "trees_fp64_dd_td_fx_fxw": stats["trees"], "tree_seconds_fp64_dd_td_fx_fxw": stats["tree_seconds"],
+            "trees_fp64_dd_td_fx_fxw_fxn": stats["trees"], "tree_seconds_fp64_dd_td_fx_fxw_fxn": stats["tree_seconds"],
             "other_seconds": stats["cond_seconds"], "fx_tuning": ctx.tuning("fx", "real"),
-            "fxw_tuning": ctx.tuning("fxw", "real"),
+            "fxw_tuning": ctx.tuning("fxw", "real"), "fxn_tuning": ctx.tuning("fxn", "real"),
             "p0_range": [float(p0.min()), float(p0.max())], "status": status,
             "workload": "M=800 modes, r~U[0.3,0.9], Haar seed 2, eta=1; %d forced trajectories with 20 uniform "
                         "click positions; no-click probability at every one of the 800 steps" % n_traj}
@@ -306,6 +307,7 @@ def walltime_block(ctx, gbs, gi, ms):
     m clicks at uniformly random positions, run together (the paper's typical case)."""
     paper = {10: (0.11, 1), 12: (0.68, 4), 14: (0.97, 32), 16: (1.98, 128), 18: (1.90, 1024), 20: (1.83, 8192)}
     # one trajectory: each step is a single tree of up to m + 1 modes
+    ctx.autotune("fxn", "real", max(ms) + 1)
     ctx.autotune("fx", "real", max(ms) + 1)
     ctx.autotune("fxw", "real", max(ms) + 1)
     rows = []
@@ -325,7 +327,7 @@ def walltime_block(ctx, gbs, gi, ms):
         st.free()
         rows.append({"m": m, "modes": int(stp.U.shape[0]), "seconds_per_sample": dt, "status": status,
                      "random_positions_seconds_per_sample": dt_r, "random_positions_status": status_r,
-                     "trees_fp64_dd_td_fx_fxw": stats["trees"], "tree_seconds_fp64_dd_td_fx_fxw": stats["tree_seconds"],
+                     "trees_fp64_dd_td_fx_fxw_fxn": stats["trees"], "tree_seconds_fp64_dd_td_fx_fxw_fxn": stats["tree_seconds"],
                      "escalations": stats["escalations"], "uncertified_steps": stats["uncertified"],
                      "p0_min": float(p0.min()),
                      "paper_titan_hours": paper[m][0], "paper_titan_nodes": paper[m][1]})

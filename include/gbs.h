@@ -59,7 +59,7 @@ typedef int gbs_status;
 
 /* Per-term arithmetic of the subset enumeration. */
 typedef enum {
-  GBS_PREC_AUTO = 0,       /* cheapest of FP64 / FP64P / FX / FXW / TD whose error estimate
+  GBS_PREC_AUTO = 0,       /* cheapest of FP64 / FP64P / FXN / FX / FXW / TD whose error estimate
                               meets rel_tol (FP64P only where FP64 missed by <= 1e3) */
   GBS_PREC_FP64 = 1,       /* IEEE double */
   GBS_PREC_DD = 2,         /* double-double, ~106-bit significand */
@@ -71,7 +71,7 @@ typedef enum {
                               (otherwise GBS_EPRECISION, or TD under AUTO) */
   GBS_PREC_FXW = 6,        /* wide fixed point, 256-bit integers: 192 fraction bits,
                               same range and conditions as GBS_PREC_FX */
-  GBS_PREC_FP64P = 7       /* FP64 with the last two levels of the subset tree summed
+  GBS_PREC_FP64P = 7,      /* FP64 with the last two levels of the subset tree summed
                               in a cancellation-free form: each group of four subsets
                               that differ only in the last two modes adds one value
                               whose factors carry small relative errors, so the
@@ -79,6 +79,10 @@ typedef enum {
                               the terms' (1e2..1e3 smaller on Haar states).  Real
                               basis; Torontonians only (not the sampler's split sums).
                               abs_sum / kappa then refer to the group magnitudes. */
+  GBS_PREC_FXN = 8         /* narrow fixed point, 160-bit integers: 128 fraction bits,
+                              same range and conditions as GBS_PREC_FX, ~0.7x its
+                              integer work; tried before FX where a prediction of the
+                              cancellation says it suffices */
 } gbs_prec;
 
 /* Basis of the matrices the enumeration factors.  Both give identical
@@ -199,8 +203,8 @@ typedef struct {
   long long near_ties;    /* coin draws with |u - p0| < 1e-9 */
   long long rejections;   /* trajectories abandoned by postselection (each may retry) */
   double seconds;         /* wall time of the call */
-  long long trees[5];     /* subset trees evaluated in FP64, DD, TD, FX, FXW */
-  double tree_seconds[5]; /* wall time spent in those tree batches */
+  long long trees[6];     /* subset trees evaluated in FP64, DD, TD, FX, FXW, FXN */
+  double tree_seconds[6]; /* wall time spent in those tree batches */
   double cond_seconds;    /* wall time of gathers, decisions and conditioning */
   long long uncertified;  /* steps whose p0 error bound stayed above 5e-10 even in TD */
 } gbs_sample_stats;

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libgbs.so")
 HEADER = os.path.join(HERE, "..", "include", "gbs.h")
 
 OK, EINVAL, ENOMEM, ENOTPD, EPRECISION, EREJECT, ETIMEDOUT, ECUDA, PENDING, ENOTFOUND = range(10)
-PREC = {"auto": 0, "fp64": 1, "dd": 2, "td": 3, "fp32": 4, "fx": 5, "fxw": 6, "fp64p": 7}
+PREC = {"auto": 0, "fp64": 1, "dd": 2, "td": 3, "fp32": 4, "fx": 5, "fxw": 6, "fp64p": 7, "fxn": 8}
 PREC_NAME = {v: k for k, v in PREC.items()}
 BASIS = {"auto": 0, "real": 1, "complex": 2}
 BASIS_NAME = {v: k for k, v in BASIS.items()}
@@ -43,7 +43,7 @@ class gbs_prob(ctypes.Structure):
 class gbs_sample_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("escalations", ctypes.c_longlong),
                 ("near_ties", ctypes.c_longlong), ("rejections", ctypes.c_longlong), ("seconds", ctypes.c_double),
-                ("trees", ctypes.c_longlong * 5), ("tree_seconds", ctypes.c_double * 5),
+                ("trees", ctypes.c_longlong * 6), ("tree_seconds", ctypes.c_double * 6),
                 ("cond_seconds", ctypes.c_double), ("uncertified", ctypes.c_longlong)]
 
 

@@ -212,6 +212,8 @@ gbs_status gbs_ctx_create(gbs_ctx** out, int device, size_t hbm_budget_bytes) {
     ctx->tune[GBS_PREC_FXW][b].d_top = 6;
     ctx->tune[GBS_PREC_FP64P][b].sub_e = 6;
     ctx->tune[GBS_PREC_FP64P][b].d_top = 8;
+    ctx->tune[GBS_PREC_FXN][b].sub_e = 6;
+    ctx->tune[GBS_PREC_FXN][b].d_top = 6;
   }
   *out = ctx;
   return GBS_OK;
@@ -342,7 +344,7 @@ gbs_status gbs_torontonian(gbs_ctx* ctx, const gbs_state* st, const int* modes, 
   cudaSetDevice(ctx->device);
   gbs_status e;
   if ((e = validate_modes(ctx, modes, N, st->M))) return e;
-  if (prec < GBS_PREC_AUTO || prec > GBS_PREC_FP64P) return set_error(ctx, GBS_EINVAL, "bad precision");
+  if (prec < GBS_PREC_AUTO || prec > kPrecLast) return set_error(ctx, GBS_EINVAL, "bad precision");
   const int* mp[1] = {modes};
   const int Nv[1] = {N};
   return probs_batch(ctx, 1, &st, mp, Nv, prec, basis, rel_tol, out);
@@ -351,11 +353,11 @@ gbs_status gbs_torontonian(gbs_ctx* ctx, const gbs_state* st, const int* modes, 
 gbs_status gbs_subset_sum(gbs_ctx* ctx, int n, const double* G, int basis, int prec, double* inc, double* exc,
                           double* tor, double* abs_sum) {
   if (!ctx || !G || n < 1 || n > 32) return GBS_EINVAL;
-  if (prec < GBS_PREC_FP64 || prec > GBS_PREC_FP64P) return GBS_EINVAL;
+  if (prec < GBS_PREC_FP64 || prec > kPrecLast) return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
   cudaSetDevice(ctx->device);
   const bool real = basis != GBS_BASIS_COMPLEX;
-  if (prec == GBS_PREC_FX || prec == GBS_PREC_FXW) {
+  if (is_fixed_point(prec)) {
     double lmin = 0.0, lmax = 0.0;
     // entries and their scaled pivot inverses stay below 2^31: eigenvalues in [2^-8, 64]
     if (!real || !sym_eig_range(G, 2 * n, lmin, lmax) || !(lmin >= 0x1p-8 && lmax <= 64.0) ||

@@ -45,7 +45,7 @@ gbs_status stage(gbs_ctx* ctx, const void* data, size_t bytes, const void** dev)
 }
 
 const BatchTune& batch_tune_for(gbs_ctx* ctx, int prec, bool real) {
-  return ctx->tune[prec < 0 || prec > GBS_PREC_FP64P ? 1 : prec][real ? 1 : 0];
+  return ctx->tune[prec < 0 || prec > kPrecLast ? 1 : prec][real ? 1 : 0];
 }
 
 // Every value of a tree over n modes of (Sigma^-1)_S fits the fixed-point
@@ -178,6 +178,7 @@ static double unit_roundoff_b(int prec) {
     case GBS_PREC_DD: return ldexp(1.0, -102);
     case GBS_PREC_TD: return ldexp(1.0, -152);
     case GBS_PREC_FP32_DIAG: return ldexp(1.0, -24);
+    case GBS_PREC_FXN: return ldexp(1.0, -108);
     case GBS_PREC_FX: return ldexp(1.0, -140);
     case GBS_PREC_FXW: return ldexp(1.0, -158);  // the three-double output, not the 2^-192 resolution, limits it
   }
@@ -199,6 +200,8 @@ static gbs_status batch_variant(gbs_ctx* ctx, int prec, bool real, int nt, const
     case GBS_PREC_FX: return real ? batch_fx_real(ctx, nt, tr, roots, outs, status, tu)
                                   : set_error(ctx, GBS_EINVAL, "the fixed-point precision needs the real basis");
     case GBS_PREC_FXW: return real ? batch_fxw_real(ctx, nt, tr, roots, outs, status, tu)
+                                   : set_error(ctx, GBS_EINVAL, "the fixed-point precision needs the real basis");
+    case GBS_PREC_FXN: return real ? batch_fxn_real(ctx, nt, tr, roots, outs, status, tu)
                                    : set_error(ctx, GBS_EINVAL, "the fixed-point precision needs the real basis");
     case GBS_PREC_FP64P: return real ? batch_fp64p_real(ctx, nt, tr, roots, outs, status, tu)
                                      : set_error(ctx, GBS_EINVAL, "the paired FP64 precision needs the real basis");
@@ -322,11 +325,15 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
   // states it was measured on); then fixed point (160, then 192 fraction bits) where the
   // state bounds the tree (real basis), then triple-double.  A request moves
   // on while its error estimate misses rel_tol or its fixed-point tree left the
-  // range.
+  // range.  The narrow fixed point (128 fraction bits) comes before FX for the
+  // requests whose earlier rungs bound |p| away from zero well enough to
+  // predict its estimate (FP64's scaled by 2^-55) within rel_tol with a factor
+  // 2 of margin; without such a bound a miss would cost ~0.7 of FX on top.
   constexpr double kPairReach = 1e3;
-  const int ladder[5] = {GBS_PREC_FP64, GBS_PREC_FP64P, GBS_PREC_FX, GBS_PREC_FXW, GBS_PREC_TD};
-  const int steps = prec == GBS_PREC_AUTO ? 5 : 1;
+  const int ladder[6] = {GBS_PREC_FP64, GBS_PREC_FP64P, GBS_PREC_FXN, GBS_PREC_FX, GBS_PREC_FXW, GBS_PREC_TD};
+  const int steps = prec == GBS_PREC_AUTO ? 6 : 1;
   bool uncertified = false;
+  std::vector<double> err64(nreq, INFINITY), p_low(nreq, 0.0);  // FP64 estimate, lower bound on |p|
   for (int k = 0; k < steps && !todo.empty(); ++k) {
     const int pr = prec == GBS_PREC_AUTO ? ladder[k] : prec;
     std::vector<int> run, next;
@@ -336,7 +343,11 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
         next.push_back(i);
         continue;
       }
-      if ((pr == GBS_PREC_FX || pr == GBS_PREC_FXW) && !(real && fx_ok_inverse(states[i], N[i]))) {
+      if (prec == GBS_PREC_AUTO && pr == GBS_PREC_FXN && !(2.0 * err64[i] * 0x1p-55 <= tol * p_low[i])) {
+        next.push_back(i);
+        continue;
+      }
+      if (is_fixed_point(pr) && !(real && fx_ok_inverse(states[i], N[i]))) {
         if (prec == GBS_PREC_AUTO) {
           next.push_back(i);
           continue;
@@ -357,6 +368,8 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
     for (size_t i = 0; i < run.size(); ++i) {
       fill(&out[run[i]], res[i], pr, real, ld[i]);
       if (prec != GBS_PREC_AUTO) continue;
+      if (pr == GBS_PREC_FP64) err64[run[i]] = res[i].err;
+      if (res[i].status == 0) p_low[run[i]] = std::max(p_low[run[i]], fabs(res[i].p_hi) - res[i].err);
       const bool missed = res[i].status == 0 && !(res[i].err <= tol * fabs(res[i].p_hi));
       // triple-double (u = 2^-152) cannot improve on a wide fixed-point result
       // (2^-158): such a request stops here, uncertified
@@ -383,7 +396,7 @@ using namespace gbs;
 
 extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, int n_trees, char* report,
                                    size_t report_len) {
-  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP64P || n < 6 || n > 28 || n_trees < 1 || n_trees > 64)
+  if (!ctx || prec < GBS_PREC_FP64 || prec > kPrecLast || n < 6 || n > 28 || n_trees < 1 || n_trees > 64)
     return GBS_EINVAL;
   if (prec >= GBS_PREC_FX && basis == GBS_BASIS_COMPLEX) return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
@@ -472,7 +485,7 @@ done:
 
 extern "C" gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub_e, int* d_top, int* grid_per_sm,
                                      long long* level_threads, int* q_drop, int* mid_e) {
-  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP64P) return GBS_EINVAL;
+  if (!ctx || prec < GBS_PREC_FP64 || prec > kPrecLast) return GBS_EINVAL;
   const BatchTune& t = ctx->tune[prec][basis != GBS_BASIS_COMPLEX ? 1 : 0];
   if (sub_e) *sub_e = t.sub_e;
   if (d_top) *d_top = t.d_top;
@@ -485,7 +498,7 @@ extern "C" gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub
 
 extern "C" gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_top, int grid_per_sm,
                                      long long level_threads, int q_drop, int mid_e) {
-  if (!ctx || prec < GBS_PREC_FP64 || prec > GBS_PREC_FP64P || sub_e < 0 || sub_e > 7 ||
+  if (!ctx || prec < GBS_PREC_FP64 || prec > kPrecLast || sub_e < 0 || sub_e > 7 ||
       (sub_e > 0 && sub_e < 5) || d_top < 0 ||
       d_top > 16 || grid_per_sm < 0 || level_threads < 1 || q_drop < 0 || q_drop > 2 || mid_e < 0 || mid_e > 8)
     return GBS_EINVAL;
@@ -504,7 +517,7 @@ extern "C" gbs_status gbs_torontonian_batch(gbs_ctx* ctx, int n_req, const gbs_s
                                             const int* modes, const int* N_per, int prec, int basis, double rel_tol,
                                             gbs_prob* out) {
   if (!ctx || n_req < 0 || (n_req > 0 && (!states || !N_per || !out))) return GBS_EINVAL;
-  if (prec < GBS_PREC_AUTO || prec > GBS_PREC_FP64P) return GBS_EINVAL;
+  if (prec < GBS_PREC_AUTO || prec > kPrecLast) return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
   cudaSetDevice(ctx->device);
   std::vector<const int*> mp(n_req);

@@ -9,8 +9,9 @@
 // the matrix entries and the scalars derived from them (pivots, determinants,
 // inverse square roots) need only 31 integer bits, the running product s of
 // pivot factors and the sums of terms need 63:
-//   FX    entries fx  = fxn<6, 5>, s and sums fxs  = fxn<7, 5>  (160 fraction bits)
-//   FXW   entries fxw = fxn<7, 6>, s and sums fxws = fxn<8, 6>  (192 fraction bits)
+//   FXN   entries fxn4 = fxn<5, 4>, s and sums fxn4s = fxn<6, 4>  (128 fraction bits)
+//   FX    entries fx   = fxn<6, 5>, s and sums fxs   = fxn<7, 5>  (160 fraction bits)
+//   FXW   entries fxw  = fxn<7, 6>, s and sums fxws  = fxn<8, 6>  (192 fraction bits)
 // Additions are exact (one carry-chained instruction per limb); a product
 // keeps the columns at and above the fraction point of the exact 2L-limb
 // product, which leaves an error of at most 2L units of the last place,
@@ -37,6 +38,8 @@ struct fxn {
   static_assert(F >= 3 && L > F, "at least three fraction limbs and one integer limb");
   uint32_t w[L];
 };
+typedef fxn<5, 4> fxn4;  // FXN entries
+typedef fxn<6, 4> fxn4s; // FXN s and sums
 typedef fxn<6, 5> fx;    // FX entries
 typedef fxn<7, 5> fxs;   // FX s and sums
 typedef fxn<7, 6> fxw;   // FXW entries
@@ -200,6 +203,8 @@ GBS_HD fxn<L, F> fx_from_double(double x) {
   }
   return (bits >> 63) ? -r : r;
 }
+template <> GBS_HD fxn4 from_double<fxn4>(double x) { return fx_from_double<5, 4>(x); }
+template <> GBS_HD fxn4s from_double<fxn4s>(double x) { return fx_from_double<6, 4>(x); }
 template <> GBS_HD fx from_double<fx>(double x) { return fx_from_double<6, 5>(x); }
 template <> GBS_HD fxs from_double<fxs>(double x) { return fx_from_double<7, 5>(x); }
 template <> GBS_HD fxw from_double<fxw>(double x) { return fx_from_double<7, 6>(x); }
@@ -211,9 +216,11 @@ GBS_HD double to_double(const fxn<L, F>& a) {
   double v = (double)(int32_t)a.w[L - 1];
 #pragma unroll
   for (int k = L - 2; k >= 0; --k) v = fma(v, 4294967296.0, (double)a.w[k]);
-  return v * (F == 5 ? 0x1p-160 : 0x1p-192);
+  return v * (F == 4 ? 0x1p-128 : F == 5 ? 0x1p-160 : 0x1p-192);
 }
-static_assert(sizeof(fx) == 24 && sizeof(fxs) == 28 && sizeof(fxw) == 28 && sizeof(fxws) == 32, "fx widths");
+static_assert(sizeof(fxn4) == 20 && sizeof(fxn4s) == 24 && sizeof(fx) == 24 && sizeof(fxs) == 28 &&
+                  sizeof(fxw) == 28 && sizeof(fxws) == 32,
+              "fx widths");
 
 // ------------------------------------------------------ tree interface ----
 template <int L, int F> GBS_HD fxn<L, F> fms(const fxn<L, F>& x, const fxn<L, F>& a, const fxn<L, F>& b) {
@@ -222,10 +229,13 @@ template <int L, int F> GBS_HD fxn<L, F> fms(const fxn<L, F>& x, const fxn<L, F>
 template <int L, int F> GBS_HD fxn<L, F> fpa(const fxn<L, F>& x, const fxn<L, F>& a, const fxn<L, F>& b) {
   return x + a * b;
 }
+template <> GBS_HD fxn4 scale_<fxn4, fxn4>(const fxn4& x, const fxn4& s) { return x * s; }
 template <> GBS_HD fx scale_<fx, fx>(const fx& x, const fx& s) { return x * s; }
 template <> GBS_HD fxw scale_<fxw, fxw>(const fxw& x, const fxw& s) { return x * s; }
+template <> GBS_HD fxn4 conv_entry<fxn4>(const double& x) { return from_double<fxn4>(x); }
 template <> GBS_HD fx conv_entry<fx>(const double& x) { return from_double<fx>(x); }
 template <> GBS_HD fxw conv_entry<fxw>(const double& x) { return from_double<fxw>(x); }
+template <> struct scale_of<fxn4> { typedef fxn4s type; };
 template <> struct scale_of<fx> { typedef fxs type; };
 template <> struct scale_of<fxw> { typedef fxws type; };
 
@@ -241,6 +251,8 @@ GBS_HD bool fx_det_in_range(const fxn<L, F>& d) {
 }
 template <int L, int F> GBS_HD bool not_positive(const fxn<L, F>& d) { return !fx_det_in_range(d); }
 template <int L, int F> GBS_HD bool is_pos(const fxn<L, F>& d) { return fx_det_in_range(d); }
+template <> constexpr int bad_status<fxn4>() { return kStatusRange; }
+template <> struct level_min_blocks<fxn4> { static const int value = 3; };
 template <> constexpr int bad_status<fx>() { return kStatusRange; }
 template <> struct level_min_blocks<fx> { static const int value = 3; };
 template <> struct level_min_blocks<fxw> { static const int value = 3; };
@@ -298,11 +310,12 @@ __device__ __forceinline__ fxn<L, F> mul_short(const fxn<L, F>& a, const fxn<L, 
 // value of the integer limb and the three fraction limbs below it (~53 bits);
 // y0 lies in (2^-6, 2^10], so its bits sit in limbs F-2 .. F.  Then, with
 // e = 1 - x y0^2 (|e| < 2^-50):
-//   160 fraction bits: one third-order step y0 (1 + e/2 + 3 e^2 / 8), whose
-//     remaining error 5 e^3 / 16 is below 2^-155 relative; e^2 comes from the
-//     double of e (the signed 64-bit integer of limbs F-2, F-3 plus limb F-4:
-//     e to 2^-128, so e^2 to 2^-175), and every product has y0 as its short
-//     factor (y0^2 is exact, so x y0^2 is truncated once);
+//   128 and 160 fraction bits: one third-order step y0 (1 + e/2 + 3 e^2 / 8),
+//     whose remaining error 5 e^3 / 16 is below 2^-155 relative; e^2 comes
+//     from the double of e (the signed 64-bit integer of limbs F-2, F-3 plus
+//     limb F-4: e to 2^-(32 F - 32), so e^2 to 2^-143 or better), and every
+//     product has y0 as its short factor (y0^2 is exact, so x y0^2 is
+//     truncated once);
 //   192 fraction bits: two Newton steps y <- y + y (1 - x y^2) / 2.
 template <int L, int F>
 __device__ __forceinline__ fxn<L, F> rsqrt_(const fxn<L, F>& x) {
@@ -312,7 +325,7 @@ __device__ __forceinline__ fxn<L, F> rsqrt_(const fxn<L, F>& x) {
   fxn<L, F> one;
 #pragma unroll
   for (int k = 0; k < L; ++k) one.w[k] = k == F ? 1u : 0u;
-  if constexpr (F == 5) {
+  if constexpr (F <= 5) {
     // y0^2 has ~106 bits, all above 2^-117: exact in the window
     const fxn<L, F> y2 = mul_short<F - 2, F, L, F, F - 2, F>(y0, y0);
     const fxn<L, F> e = one - mul_short<F - 4, F>(x, y2);
@@ -332,6 +345,7 @@ __device__ __forceinline__ fxn<L, F> rsqrt_(const fxn<L, F>& x) {
 }
 
 // ------------------------------------------------------ sums and reduction --
+template <> struct acc_traits<fxn4> { typedef fxn4s Acc; typedef fxn4s Red; };
 template <> struct acc_traits<fx> { typedef fxs Acc; typedef fxs Red; };
 template <> struct acc_traits<fxw> { typedef fxws Acc; typedef fxws Red; };
 template <int L, int F> GBS_HD void acc_add(fxn<L, F>& a, const fxn<L, F>& x) { a = a + x; }
@@ -340,6 +354,7 @@ GBS_HD void acc_fpa(fxn<L + 1, F>& acc, const fxn<L + 1, F>& s, const fxn<L, F>&
 template <int L, int F> GBS_HD fxn<L, F> red_diff(const fxn<L, F>& a, const fxn<L, F>& b, fxn<L, F>*) { return a - b; }
 template <int L, int F> GBS_HD fxn<L, F> red_add(const fxn<L, F>& a, const fxn<L, F>& b) { return a + b; }
 template <int L, int F> GBS_HD fxn<L, F> red_neg(const fxn<L, F>& a) { return -a; }
+template <> GBS_HD fxn4s red_zero<fxn4s>() { return from_double<fxn4s>(0.0); }
 template <> GBS_HD fxs red_zero<fxs>() { return from_double<fxs>(0.0); }
 template <> GBS_HD fxws red_zero<fxws>() { return from_double<fxws>(0.0); }
 // Three doubles whose sum is the value to ~2^-159 relative (each the nearest

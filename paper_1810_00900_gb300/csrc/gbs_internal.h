@@ -12,6 +12,14 @@
 
 namespace gbs {
 
+// The largest gbs_prec value.
+constexpr int kPrecLast = GBS_PREC_FXN;
+
+// The fixed-point precisions (real basis; need a state that bounds the tree).
+constexpr bool is_fixed_point(int prec) {
+  return prec == GBS_PREC_FXN || prec == GBS_PREC_FX || prec == GBS_PREC_FXW;
+}
+
 struct TreeOut;
 
 // One tree of a batch: n modes, packed FP64 root starting at entry root_off.
@@ -81,8 +89,8 @@ struct gbs_ctx {
   int sm_count = 0;
 
   // batched-engine launch parameters per (precision, basis): [prec][real]
-  gbs::BatchTune tune[8][2];  // [gbs_prec][basis is real]
-  bool tuned[8][2] = {};
+  gbs::BatchTune tune[gbs::kPrecLast + 1][2];  // [gbs_prec][basis is real]
+  bool tuned[gbs::kPrecLast + 1][2] = {};
 
   // request loop (see gbs_server.cu)
   void* server = nullptr;
@@ -140,6 +148,7 @@ gbs_status batch_td_cplx(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*,
 gbs_status batch_fx_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 gbs_status batch_fxw_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 gbs_status batch_fp64p_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
+gbs_status batch_fxn_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 gbs_status batch_fp32_real(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 gbs_status batch_fp32_cplx(gbs_ctx*, int, const BatchTree*, const void*, TreeOut*, int*, const BatchTune&);
 

@@ -252,6 +252,7 @@ double unit_of(int prec) {
   switch (prec) {
     case GBS_PREC_FP64: return 0x1p-53;
     case GBS_PREC_DD: return 0x1p-102;
+    case GBS_PREC_FXN: return 0x1p-108;
     case GBS_PREC_FX: return 0x1p-140;
     case GBS_PREC_FXW: return 0x1p-158;  // limited by the three-double tree output
   }
@@ -260,7 +261,9 @@ double unit_of(int prec) {
 
 namespace {
 // Slot of a precision in gbs_sample_stats.trees / tree_seconds.
-int stat_slot(int prec) { return prec == GBS_PREC_FX ? 3 : prec == GBS_PREC_FXW ? 4 : prec - 1; }
+int stat_slot(int prec) {
+  return prec == GBS_PREC_FX ? 3 : prec == GBS_PREC_FXW ? 4 : prec == GBS_PREC_FXN ? 5 : prec - 1;
+}
 }  // namespace
 
 
@@ -322,18 +325,19 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
   // Bound on |delta p0|: half the near-tie threshold, so that a decision can
   // differ from an exact evaluation only for draws already counted as near ties.
   const double TOL = 5e-10;
-  // AUTO ladder: FP64, fixed point with 160 then 192 fraction bits (when the
-  // state bounds the tree), triple-double.  The prediction from the previous
-  // step keeps a factor 4 of margin for FP64; a fixed-point tree is cheap
-  // enough relative to the next rung that it is tried without margin (the
-  // check after the tree escalates it when needed).
+  // AUTO ladder: FP64, fixed point with 128, 160 then 192 fraction bits (when
+  // the state bounds the tree), triple-double.  The prediction from the
+  // previous step keeps a factor 4 of margin for FP64 and 2 for the narrow
+  // fixed point (a miss there costs ~0.7 of the next rung); the wider
+  // fixed-point trees are cheap enough relative to the next rung that they are
+  // tried without margin (the check after the tree escalates it when needed).
   auto pick = [&](const Trajectory* t, double kp, int n) {
     if (prec != GBS_PREC_AUTO) return prec;
-    const int ladder[4] = {GBS_PREC_FP64, GBS_PREC_FX, GBS_PREC_FXW, GBS_PREC_TD};
-    for (int l = 0; l < 3; ++l) {
-      const bool fixed = ladder[l] != GBS_PREC_FP64;
-      if (fixed && !fx_ok_sigma(t->st, n)) continue;
-      if (4.0 * std::max(n, 1) * unit_of(ladder[l]) * kp * (fixed ? 1.0 : 4.0) < TOL) return ladder[l];
+    const int ladder[5] = {GBS_PREC_FP64, GBS_PREC_FXN, GBS_PREC_FX, GBS_PREC_FXW, GBS_PREC_TD};
+    const double margin[4] = {4.0, 2.0, 1.0, 1.0};
+    for (int l = 0; l < 4; ++l) {
+      if (is_fixed_point(ladder[l]) && !fx_ok_sigma(t->st, n)) continue;
+      if (4.0 * std::max(n, 1) * unit_of(ladder[l]) * kp * margin[l] < TOL) return ladder[l];
     }
     return (int)GBS_PREC_TD;
   };
@@ -341,7 +345,7 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
   // where the state allows it (triple-double's bound is looser), so a half
   // tree there is only redone as a full tree in the same precision.
   auto wider = [&](const Trajectory* t, int p, int n) {
-    if (p == GBS_PREC_FP64 && fx_ok_sigma(t->st, n)) return (int)GBS_PREC_FX;
+    if ((p == GBS_PREC_FP64 || p == GBS_PREC_FXN) && fx_ok_sigma(t->st, n)) return (int)GBS_PREC_FX;
     if ((p == GBS_PREC_FX || p == GBS_PREC_FXW) && fx_ok_sigma(t->st, n)) return (int)GBS_PREC_FXW;
     return (int)GBS_PREC_TD;
   };
@@ -360,7 +364,7 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
     q.half = t->need_full ? 0 : 1;
     q.n = q.half ? t->m : t->m + 1;
     q.prec = pick(t, t->kappa_prev * (q.half ? 1.5 : 8.0), q.n);
-    if ((q.prec == GBS_PREC_FX || q.prec == GBS_PREC_FXW) && !fx_ok_sigma(t->st, q.n))
+    if (is_fixed_point(q.prec) && !fx_ok_sigma(t->st, q.n))
       return set_error(ctx, GBS_EPRECISION, "sampler: the state does not bound the fixed-point tree");
     todo[i] = i;
   }
@@ -380,7 +384,7 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
     if ((e = stage(ctx, gi.data(), gi.size() * sizeof(GatherItem), &dgi))) return e;
     gather_kernel<<<(unsigned)gi.size(), 128, 0, ctx->stream>>>((const GatherItem*)dgi, (double*)ctx->hbuf.ptr);
     count_launch(ctx);
-    for (int pv : {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_FX, GBS_PREC_FXW, GBS_PREC_TD}) {
+    for (int pv : {GBS_PREC_FP64, GBS_PREC_DD, GBS_PREC_FXN, GBS_PREC_FX, GBS_PREC_FXW, GBS_PREC_TD}) {
       std::vector<size_t> grp;
       for (size_t i : todo)
         if (trees[i].prec == pv && trees[i].n > 0) grp.push_back(i);
@@ -540,7 +544,7 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
   if (!ctx || !cst || !patterns || n_samples < 1) return GBS_EINVAL;
   if (N_post < 0 || N_post > kMaxClicks || (forced_clicks && N_post < 1)) return GBS_EINVAL;
   if (prec != GBS_PREC_AUTO && prec != GBS_PREC_FP64 && prec != GBS_PREC_DD && prec != GBS_PREC_TD &&
-      prec != GBS_PREC_FX && prec != GBS_PREC_FXW)
+      !is_fixed_point(prec))
     return GBS_EINVAL;
   if (max_attempts < 1) max_attempts = 1;
   std::lock_guard<std::mutex> g(ctx->mu);

@@ -341,7 +341,7 @@ gbs_status validate(gbs_ctx* ctx, const gbs_request* r, std::vector<int>& modes)
   if (r->kind == GBS_REQ_PROB) {
     if (r->N < 0 || r->N > 32) return set_error(ctx, GBS_EINVAL, "request: N must be in [0, 32]");
     if (r->N > 0 && !r->modes) return set_error(ctx, GBS_EINVAL, "request: modes is NULL");
-    if (r->prec < GBS_PREC_AUTO || r->prec > GBS_PREC_FP64P) return set_error(ctx, GBS_EINVAL, "request: prec");
+    if (r->prec < GBS_PREC_AUTO || r->prec > kPrecLast) return set_error(ctx, GBS_EINVAL, "request: prec");
     modes.assign(r->modes, r->modes + r->N);
     std::vector<int> s = modes;
     std::sort(s.begin(), s.end());
@@ -355,7 +355,7 @@ gbs_status validate(gbs_ctx* ctx, const gbs_request* r, std::vector<int>& modes)
     if (r->N < 0 || r->N > 31) return set_error(ctx, GBS_EINVAL, "request: N_post must be in [0, 31]");
     if (r->max_attempts < 1) return set_error(ctx, GBS_EINVAL, "request: max_attempts must be >= 1");
     if (r->prec != GBS_PREC_AUTO && r->prec != GBS_PREC_FP64 && r->prec != GBS_PREC_DD && r->prec != GBS_PREC_TD &&
-        r->prec != GBS_PREC_FX && r->prec != GBS_PREC_FXW)
+        !is_fixed_point(r->prec))
       return set_error(ctx, GBS_EINVAL, "request: prec");
     if (r->sample_index < 0 || r->sample_index >= (1 << 20)) return set_error(ctx, GBS_EINVAL, "request: sample index");
     return GBS_OK;

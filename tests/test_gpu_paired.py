@@ -134,7 +134,7 @@ def test_refusals(ctx):
 def test_auto_ladder_uses_the_paired_rung(ctx):
     # N = 8 of the 200-mode pure state: FP64's estimate (kappa ~ 7e10) misses 1e-5 by ~20x,
     # the grouped sum's meets it; at the default 1e-10 the miss exceeds 1e3 and AUTO goes on
-    # to fixed point directly
+    # to fixed point directly, the narrow width, since FP64 bounds |p| away from zero
     st_p = gi.uniform_squeezed_state(200, 0.8, seed=1)
     st = gbs.build_state(ctx, st_p.U, st_p.r, 1.0)
     modes = gi.random_modes(200, 8, seed=1)
@@ -146,5 +146,6 @@ def test_auto_ladder_uses_the_paired_rung(ctx):
     assert pr.err_bound <= 1e-5 * abs(pr.p)
     assert abs(pr.tor_value - want) <= 1e-5 * abs(want)
     pr2 = gbs.torontonian(ctx, st, modes, "auto", "real")
-    assert pr2.prec == "fx"
+    assert pr2.prec == "fxn" and pr2.err_bound <= 1e-10 * abs(pr2.p)
+    assert abs(pr2.tor_value - want) <= 1e-10 * abs(want)
     st.free()

@@ -43,7 +43,7 @@ def test_forced_trajectories_p0_every_step(ctx):
         assert np.allclose(p0[i], np.array(ref["p0"]), rtol=0, atol=1e-10), (p0[i], ref["p0"])
 
 
-@pytest.mark.parametrize("prec", ["auto", "dd", "fx", "fxw"])
+@pytest.mark.parametrize("prec", ["auto", "dd", "fxn", "fx", "fxw"])
 def test_free_samples_match_oracle(ctx, prec):
     M = 6
     st, Sig = make(ctx, M, 21, r=(0.6, 1.1), eta=0.9)
@@ -102,6 +102,9 @@ def test_forced_trajectory_fixed_point_equals_triple_double(ctx):
     _, p_fx, s_fx, st1 = gbs.sample(ctx, st, 1, seed=3, N_post=12, forced_clicks=forced, prec="fx", want_p0=True)
     _, p_td, s_td, st2 = gbs.sample(ctx, st, 1, seed=3, N_post=12, forced_clicks=forced, prec="td", want_p0=True)
     _, p_fw, s_fw, st3 = gbs.sample(ctx, st, 1, seed=3, N_post=12, forced_clicks=forced, prec="fxw", want_p0=True)
-    assert st1 == 0 and st2 == 0 and st3 == 0
+    _, p_fn, s_fn, st4 = gbs.sample(ctx, st, 1, seed=3, N_post=12, forced_clicks=forced, prec="fxn", want_p0=True)
+    assert st1 == 0 and st2 == 0 and st3 == 0 and st4 == 0
     assert np.max(np.abs(p_fx - p_td)) < 1e-20 and np.max(np.abs(p_fw - p_td)) < 1e-20
+    assert np.max(np.abs(p_fn - p_td)) < 1e-15
     assert s_fx["trees"][3] > 0 and s_fx["trees"][2] == 0 and s_td["trees"][2] > 0 and s_fw["trees"][4] > 0
+    assert s_fn["trees"][5] > 0
