@@ -528,7 +528,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "dd", "td", "fp32", "fx", "fxw"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp64p", "dd", "td", "fp32", "fxn", "fx", "fxw"])
     ap.add_argument("--basis", default="real", choices=["real", "complex"])
     ap.add_argument("--N", type=int, default=24)
     ap.add_argument("--cpu-sample", type=int, default=19, help="click count of the oracle's CPU sample")
@@ -584,7 +584,7 @@ def main():
     tuning = ctx.tuning(args.prec, args.basis)
     Q = {("fp64", False): 5, ("fp64", True): 4, ("dd", False): 4, ("dd", True): 3, ("td", False): 3,
          ("td", True): 2, ("fp32", False): 5, ("fp32", True): 4, ("fx", False): 3,
-         ("fxw", False): 3}[(args.prec, complex_basis)]
+         ("fxw", False): 3, ("fp64p", False): 5, ("fxn", False): 3}[(args.prec, complex_basis)]
     Q = max(1, min(Q - tuning["q_drop"], args.N))
     q_root = min(args.N, Q + tuning["sub_e"])
     depth = args.N - q_root

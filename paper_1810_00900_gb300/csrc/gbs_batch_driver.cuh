@@ -210,23 +210,23 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
     const int ns = sub_e > 0 ? (int)subs[qv].size() : (int)leaf[qv].size();
     Partial<Red>* pp = parts + part_base[qv];
     switch (qv) {
-#define GBS_LEAF_CASE(QQ)                                                                                       \
-  case QQ:                                                                                                      \
-    if constexpr (QQ <= QMAX) {                                                                                 \
-      if (sub_e > 0) {                                                                                          \
-        if ((st = check_cuda(ctx,                                                                               \
-                             cudaFuncSetAttribute(batch_subtree_kernel<E, QQ, PAIR>,                                  \
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sub), \
-                             "subtree smem")))                                                                  \
-          return st;                                                                                            \
-        batch_subtree_kernel<E, QQ, PAIR><<<(unsigned)grid, nthr, smem_sub, s>>>(                                    \
-            (const SubSeg*)(plan + o_leaf[qv]), ns, nb, buf[0], buf[1], sb[0], sb[1], capA, capB, pp,           \
-            status_dev);                                                                                        \
-      } else {                                                                                                  \
-        batch_leaf_kernel<E, QQ, PAIR><<<(unsigned)grid, 128, 0, s>>>((const LeafSeg*)(plan + o_leaf[qv]), ns, nb,   \
-                                                                buf[0], buf[1], sb[0], sb[1], pp, status_dev);  \
-      }                                                                                                         \
-    }                                                                                                           \
+#define GBS_LEAF_CASE(QQ)                                                                                              \
+  case QQ:                                                                                                             \
+    if constexpr (QQ <= QMAX) {                                                                                        \
+      if (sub_e > 0) {                                                                                                 \
+        if ((st = check_cuda(ctx,                                                                                      \
+                             cudaFuncSetAttribute(batch_subtree_kernel<E, QQ, PAIR>,                                   \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sub),         \
+                             "subtree smem")))                                                                         \
+          return st;                                                                                                   \
+        batch_subtree_kernel<E, QQ, PAIR><<<(unsigned)grid, nthr, smem_sub, s>>>(                                      \
+            (const SubSeg*)(plan + o_leaf[qv]), ns, nb, buf[0], buf[1], sb[0], sb[1], capA, capB, pp,                  \
+            status_dev);                                                                                               \
+      } else {                                                                                                         \
+        batch_leaf_kernel<E, QQ, PAIR><<<(unsigned)grid, 128, 0, s>>>((const LeafSeg*)(plan + o_leaf[qv]), ns, nb,     \
+                                                                buf[0], buf[1], sb[0], sb[1], pp, status_dev);         \
+      }                                                                                                                \
+    }                                                                                                                  \
     break;
       GBS_LEAF_CASE(1)
       GBS_LEAF_CASE(2)
