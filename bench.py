@@ -659,7 +659,8 @@ def main():
             "workload": "single Torontonian, N=%d clicks of the M=200 pure state (r=0.8, Haar seed 1): "
                         "2^%d subset determinants per step" % (args.N, args.N),
             "M": 200, "N": args.N, "basis": args.basis, "per_term_arithmetic": args.prec,
-            "sum": {"fp64": "double-double", "dd": "double-double", "fp32": "double-double", "td": "triple-double",
+            "sum": {"fp64": "double-double", "fp64p": "double-double", "dd": "double-double",
+                    "fp32": "double-double", "td": "triple-double", "fxn": "exact fixed point",
                     "fx": "exact fixed point", "fxw": "exact fixed point"}[args.prec],
             "l2": "flushed between steps (256 MB write); tree level buffers also exceed L2",
             "parallelism": "replicas" if ws > 1 else "single GPU",
