@@ -14,7 +14,7 @@
 //   FXW   entries fxw  = fxn<7, 6>, s and sums fxws  = fxn<8, 6>  (192 fraction bits)
 // Additions are exact (one carry-chained instruction per limb); a product
 // keeps the columns at and above the fraction point of the exact 2L-limb
-// product, which leaves an error of at most 2L units of the last place,
+// product, which leaves an error of at most F units of the last place,
 // biased low.
 //
 // Inside the tree every value stays in range when the caller has checked it:
@@ -116,63 +116,56 @@ GBS_HD fxn<L + 1, F> fx_widen(const fxn<L, F>& a) {
 }
 
 // ---------------------------------------------------------------- product --
-// Window of the unsigned product: columns F to F + L - 1.  Low halves of the
-// partial products a_i b_j with i + j >= F and high halves with i + j >= F - 1
-// are summed in two arrays; in either array the carry out of row i lands in a
-// column that no earlier row has reached, so one add captures it.  The low
-// halves of column F - 1 and everything below are dropped: at most 2L units of
-// the last place, always toward -inf.  The two's-complement correction
-// subtracts b (resp. a) shifted by L limbs when a (resp. b) is negative.
+// Window of the unsigned product: columns F to F + L - 1, plus a guard column
+// F - 1.  Row by row (operand a_i against the limbs of b that reach the
+// window), each partial product is added to its column together with the
+// running carry as one 64-bit multiply-add, whose high word is the next
+// carry; a row's final carry lands in the column one past its last product,
+// which no earlier row has reached (rows whose last product is the top
+// column drop it: the arithmetic is modulo 2^(32 L)).  Partial products below
+// the guard column are not formed and the guard column is dropped: at most F
+// units of the last place, always toward -inf.  The two's-complement
+// correction subtracts b (resp. a) shifted by L limbs when a (resp. b) is
+// negative.
 template <int L, int F>
 GBS_HD fxn<L, F> operator*(const fxn<L, F>& a, const fxn<L, F>& b) {
-  constexpr int W = L, C0 = F;  // C0: column of word 0
-  uint32_t lo[W], hi[W];
+  constexpr int W = L, G = F - 1;  // G: column of r[0] (the guard)
+  uint32_t r[W + 1];
 #pragma unroll
-  for (int k = 0; k < W; ++k) lo[k] = hi[k] = 0u;
+  for (int k = 0; k <= W; ++k) r[k] = 0u;
 #pragma unroll
   for (int i = 0; i < L; ++i) {
-    {  // lo(a_i b_j) -> column i + j, for columns C0 .. C0 + W - 1
-      const int j0 = (C0 - i) > 0 ? (C0 - i) : 0;
-      const int j1 = (C0 + W - 1 - i) < (L - 1) ? (C0 + W - 1 - i) : (L - 1);
-      if (j0 <= j1) {
-        lo[i + j0 - C0] = mad_lo_cc(a.w[i], b.w[j0], lo[i + j0 - C0]);
+    const int j0 = (G - i) > 0 ? (G - i) : 0;
+    const int j1 = (G + W - i) < (L - 1) ? (G + W - i) : (L - 1);
+    if (j0 > j1) continue;
+    uint32_t carry = 0u;
 #pragma unroll
-        for (int j = j0 + 1; j <= j1; ++j) lo[i + j - C0] = madc_lo_cc(a.w[i], b.w[j], lo[i + j - C0]);
-        if (i + j1 + 1 - C0 < W) lo[i + j1 + 1 - C0] = addc(0u, 0u);
-      }
+    for (int j = j0; j <= j1; ++j) {
+      const unsigned long long t = (unsigned long long)a.w[i] * b.w[j] + r[i + j - G] + carry;
+      r[i + j - G] = (uint32_t)t;
+      carry = (uint32_t)(t >> 32);
     }
-    {  // hi(a_i b_j) -> column i + j + 1
-      const int j0 = (C0 - 1 - i) > 0 ? (C0 - 1 - i) : 0;
-      const int j1 = (C0 + W - 2 - i) < (L - 1) ? (C0 + W - 2 - i) : (L - 1);
-      if (j0 <= j1) {
-        hi[i + j0 + 1 - C0] = mad_hi_cc(a.w[i], b.w[j0], hi[i + j0 + 1 - C0]);
-#pragma unroll
-        for (int j = j0 + 1; j <= j1; ++j) hi[i + j + 1 - C0] = madc_hi_cc(a.w[i], b.w[j], hi[i + j + 1 - C0]);
-        if (i + j1 + 2 - C0 < W) hi[i + j1 + 2 - C0] = addc(0u, 0u);
-      }
-    }
+    if (i + j1 + 1 - G <= W) r[i + j1 + 1 - G] = carry;
   }
-  fxn<L, F> r;
-  r.w[0] = add_cc(lo[0], hi[0]);
+  fxn<L, F> out;
 #pragma unroll
-  for (int k = 1; k < L - 1; ++k) r.w[k] = addc_cc(lo[k], hi[k]);
-  r.w[L - 1] = addc(lo[L - 1], hi[L - 1]);
+  for (int k = 0; k < L; ++k) out.w[k] = r[k + 1];
   // signed correction: result limbs S .. L-1 (column L and up) minus masked limbs
   constexpr int S = L - F;
   const uint32_t ma = (uint32_t)((int32_t)a.w[L - 1] >> 31), mb = (uint32_t)((int32_t)b.w[L - 1] >> 31);
   if constexpr (S == L - 1) {
-    r.w[S] -= (b.w[0] & ma) + (a.w[0] & mb);
+    out.w[S] -= (b.w[0] & ma) + (a.w[0] & mb);
   } else {
-    r.w[S] = sub_cc(r.w[S], b.w[0] & ma);
+    out.w[S] = sub_cc(out.w[S], b.w[0] & ma);
 #pragma unroll
-    for (int k = S + 1; k < L - 1; ++k) r.w[k] = subc_cc(r.w[k], b.w[k - S] & ma);
-    r.w[L - 1] = subc(r.w[L - 1], b.w[L - 1 - S] & ma);
-    r.w[S] = sub_cc(r.w[S], a.w[0] & mb);
+    for (int k = S + 1; k < L - 1; ++k) out.w[k] = subc_cc(out.w[k], b.w[k - S] & ma);
+    out.w[L - 1] = subc(out.w[L - 1], b.w[L - 1 - S] & ma);
+    out.w[S] = sub_cc(out.w[S], a.w[0] & mb);
 #pragma unroll
-    for (int k = S + 1; k < L - 1; ++k) r.w[k] = subc_cc(r.w[k], a.w[k - S] & mb);
-    r.w[L - 1] = subc(r.w[L - 1], a.w[L - 1 - S] & mb);
+    for (int k = S + 1; k < L - 1; ++k) out.w[k] = subc_cc(out.w[k], a.w[k - S] & mb);
+    out.w[L - 1] = subc(out.w[L - 1], a.w[L - 1 - S] & mb);
   }
-  return r;
+  return out;
 }
 // s * g: the wide scale type times an entry scalar.
 template <int L, int F>
@@ -259,10 +252,13 @@ template <> struct level_min_blocks<fxw> { static const int value = 3; };
 template <> constexpr int bad_status<fxw>() { return kStatusRange; }
 
 // a * b where b >= 0 has nonzero limbs only in [JLO, JHI] (and, when ILO/IHI
-// are given, a >= 0 only in [ILO, IHI]): the product of the general routine
-// restricted to those rows and columns (the carry of row i still lands in
-// column i + JHI + 1, which no earlier row reached), with the one correction a
-// negative a needs.
+// are given, a >= 0 only in [ILO, IHI]), for the inverse square root's short
+// operands: low and high halves of the partial products a_i b_j that reach
+// the window (low halves from column F, high halves from column F - 1) are
+// summed in two carry-chained arrays, in either of which the carry out of row
+// i lands in column i + JHI + 1, which no earlier row reached; then the one
+// correction a negative a needs.  At most 2L units of the last place, toward
+// -inf.
 template <int JLO, int JHI, int L, int F, int ILO = 0, int IHI = L - 1>
 __device__ __forceinline__ fxn<L, F> mul_short(const fxn<L, F>& a, const fxn<L, F>& b) {
   constexpr int W = L, C0 = F;
