@@ -87,3 +87,13 @@ def test_n24_fp64_throughput_configuration_sums_all_terms(ctx_state):
         pr = gbs.torontonian(ctx, st, modes, "fp64", basis)
         assert abs(pr.abs_sum - abs_ref) <= 1e-12 * abs_ref
         assert pr.err_bound > abs(pr.p) * 1e-9  # honestly flagged as uncertified
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64p", "dd", "fxn"])
+def test_n24_error_bound_holds_in_every_precision(ctx_state, prec):
+    # the precisions that cannot certify 1e-9 at kappa ~ 1e26 still bound their own error
+    ctx, st, modes = ctx_state
+    _, _, p_ref = golden()
+    pr = gbs.torontonian(ctx, st, modes, prec, "real")
+    assert pr.prec == prec
+    assert abs(pr.p - p_ref) <= pr.err_bound, (prec, pr.p, p_ref, pr.err_bound)
