@@ -62,6 +62,36 @@ __device__ __forceinline__ int find_seg(const Seg* segs, int nseg, Key key, Key 
   return lo;
 }
 
+// Node buffers in global memory hold packed lower triangles entry-major: entry
+// e of node i of a region of `count` nodes is element e * count + i.  Multiword
+// entries (node_words > 0) are stored limb-major inside that: limb k of entry e
+// of node i is 32-bit word (e * L + k) * count + i of the region, so every limb
+// load or store of a warp covers one contiguous 128-byte line.
+template <class E>
+__device__ __forceinline__ E ld_node(const E* base, long long e, long long count, long long i) {
+  constexpr int L = node_words<E>::value;
+  if constexpr (L == 0) {
+    return base[e * count + i];
+  } else {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(base);
+    E r;
+#pragma unroll
+    for (int k = 0; k < L; ++k) r.w[k] = w[(e * L + k) * count + i];
+    return r;
+  }
+}
+template <class E>
+__device__ __forceinline__ void st_node(E* base, long long e, long long count, long long i, const E& v) {
+  constexpr int L = node_words<E>::value;
+  if constexpr (L == 0) {
+    base[e * count + i] = v;
+  } else {
+    uint32_t* w = reinterpret_cast<uint32_t*>(base);
+#pragma unroll
+    for (int k = 0; k < L; ++k) w[(e * L + k) * count + i] = v.w[k];
+  }
+}
+
 // packed index -> (row, col), col <= row
 __device__ __forceinline__ void untri(int e, int& a, int& b) {
   int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
@@ -191,7 +221,7 @@ __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
     for (int e = threadIdx.x; e < sym(dq); e += blockDim.x) {
       int a, b;
       untri(e, a, b);
-      out[sg.out_base + (long long)e * cnt + node] = C[tri(a + o, b + o)];
+      st_node(out + sg.out_base, e, cnt, node, C[tri(a + o, b + o)]);
     }
     if (threadIdx.x == 0) sout[sg.s_base + node] = s;
   } else {
@@ -218,7 +248,7 @@ __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
     const long long first = node << sg.emid;
     for (int i = threadIdx.x; i < sym(2 * q) * nodes; i += blockDim.x) {
       const int e = i / nodes, t = i - e * nodes;
-      out[sg.out_base + (long long)e * cnt + first + t] = src[i];
+      st_node(out + sg.out_base, e, cnt, first + t, src[i]);
     }
     for (int t = threadIdx.x; t < nodes; t += blockDim.x) sout[sg.s_base + first + t] = ssrc[t];
   }
@@ -243,7 +273,7 @@ __global__ void __launch_bounds__(256, level_min_blocks<E>::value) batch_level_k
   const E* par = in + sg.in_base;
   const long long c2 = 2 * count;
   E* chi = out + sg.out_base;
-#define PAR(i, j) par[(long long)tri(i, j) * count + node]
+#define PAR(i, j) ld_node(par, tri(i, j), count, node)
   const T p00 = re_of(PAR(0, 0));
   const T p11 = re_of(PAR(1, 1));
   const E p10 = PAR(1, 0);
@@ -264,14 +294,14 @@ __global__ void __launch_bounds__(256, level_min_blocks<E>::value) batch_level_k
       const E x = PAR(a + 2, b + 2);
       E v = fms_conj(x, L0, PAR(b + 2, 0));
       v = fms_conj(v, L1, PAR(b + 2, 1));
-      chi[(long long)tri(a, b) * c2 + 2 * node] = x;
-      chi[(long long)tri(a, b) * c2 + 2 * node + 1] = v;
+      st_node(chi, tri(a, b), c2, 2 * node, x);
+      st_node(chi, tri(a, b), c2, 2 * node + 1, v);
     }
     const E x = PAR(a + 2, a + 2);
     E v = fms_conj_re(x, L0, u0);
     v = fms_conj_re(v, L1, u1);
-    chi[(long long)tri(a, a) * c2 + 2 * node] = x;
-    chi[(long long)tri(a, a) * c2 + 2 * node + 1] = v;
+    st_node(chi, tri(a, a), c2, 2 * node, x);
+    st_node(chi, tri(a, a), c2, 2 * node + 1, v);
   }
   if (grp == 0) {
     const typename scale_of<E>::type s = sin[sg.s_in + node];
@@ -302,7 +332,7 @@ __global__ void __launch_bounds__(128) batch_leaf_kernel(const LeafSeg* __restri
       const E* nodes = (sg.buf ? buf1 : buf0) + sg.base;
       E c[sym(2 * Q)];
 #pragma unroll
-      for (int e = 0; e < sym(2 * Q); ++e) c[e] = nodes[(long long)e * sg.count + node];
+      for (int e = 0; e < sym(2 * Q); ++e) c[e] = ld_node(nodes, e, sg.count, node);
       const typename scale_of<E>::type s = (sg.buf ? s1 : s0)[sg.s_base + node];
       if (!subtree_sums<E, Q, PAIR>(c, s, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
       if ((sg.depth - __popcll((unsigned long long)node)) & 1) {
@@ -352,7 +382,7 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
     const long long root = vb - sg.block_begin;
     const E* rsrc = (sg.buf ? buf1 : buf0) + sg.base;
     int q = sg.q_root;
-    for (int e = threadIdx.x; e < sym(2 * q); e += nthr) bufA[e] = rsrc[(long long)e * sg.count + root];
+    for (int e = threadIdx.x; e < sym(2 * q); e += nthr) bufA[e] = ld_node(rsrc, e, sg.count, root);
     if (threadIdx.x == 0) sA[0] = (sg.buf ? s1 : s0)[sg.s_base + root];
     __syncthreads();
     E* src = bufA;

@@ -68,6 +68,10 @@ template <class E> struct scale_of { typedef typename real_of<E>::type type; };
 // too few warps otherwise.
 template <class E> struct level_min_blocks { static const int value = 1; };
 
+// 32-bit words of a multiword entry stored limb by limb in the global node
+// buffers of the batched engine (0: the entry is stored whole).
+template <class E> struct node_words { static const int value = 0; };
+
 // ------------------------------------------------ accumulation types -----
 // Per-thread accumulators (Acc) and cross-thread reduction values (Red).
 template <class T> struct acc_traits;

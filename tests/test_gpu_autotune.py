@@ -51,7 +51,9 @@ def test_launch_shapes_agree(ctx):
 def test_autotune_picks_a_candidate(ctx):
     rep = ctx.autotune("fp64", "real", 14)
     assert len(rep) >= 8 and all(r["ms"] > 0 for r in rep)
-    best = min(rep, key=lambda r: r["ms"])
+    best = min(r["ms"] for r in rep)
     t = ctx.tuning("fp64", "real")
-    keys = ("sub_e", "d_top", "grid_per_sm", "q_drop", "mid_e")
-    assert tuple(t[k] for k in keys) == tuple(best[k] for k in keys)
+    keys = ("sub_e", "d_top", "grid_per_sm", "level_threads", "q_drop", "mid_e")
+    chosen = [r for r in rep if all(r[k] == t[k] for k in keys)]
+    # the report rounds to 0.1 us, so several candidates can tie with the one kept
+    assert len(chosen) == 1 and chosen[0]["ms"] == best
