@@ -146,6 +146,35 @@ __global__ void batch_click_block_kernel(const ClickReq* __restrict__ reqs, int 
   }
 }
 
+// A-priori cancellation estimate of each tree: the ratio sum|t| / |Tor| the
+// modes would have if they were independent, prod_j (g_j + 1) / |g_j - 1| with
+// g_j = det(P_j)^(-1/2) of the mode's diagonal 2x2 block of the root (exact
+// for independent modes; on Haar-random states it lies 0.3 to 17 orders of
+// magnitude above the true ratio).  Output: log10 of it per tree (inf when a
+// block has g = 1 or is not positive definite).
+__global__ void kappa_estimate_kernel(const BatchTree* __restrict__ trees, int ntrees, const void* __restrict__ roots,
+                                      int real_basis, double* __restrict__ log10_kappa) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntrees) return;
+  const BatchTree tr = trees[t];
+  double lk = 0.0;
+  for (int j = 0; j < tr.n; ++j) {
+    const long long a = (long long)(2 * j) * (2 * j + 1) / 2 + 2 * j;        // tri(2j, 2j)
+    const long long b = (long long)(2 * j + 1) * (2 * j + 2) / 2 + 2 * j;    // tri(2j+1, 2j)
+    double det;
+    if (real_basis) {
+      const double* r = (const double*)roots + tr.root_off;
+      det = r[a] * r[b + 1] - r[b] * r[b];
+    } else {
+      const cplx<double>* r = (const cplx<double>*)roots + tr.root_off;
+      det = r[a].re * r[b + 1].re - (r[b].re * r[b].re + r[b].im * r[b].im);
+    }
+    const double g = det > 0.0 ? rsqrt(det) : 0.0;
+    lk += det > 0.0 && g != 1.0 ? log10((g + 1.0) / fabs(g - 1.0)) : INFINITY;
+  }
+  log10_kappa[t] = lk;
+}
+
 __global__ void batch_finish_kernel(const TreeOut* __restrict__ outs, const int* __restrict__ status,
                                     const double* __restrict__ logdet, const int* __restrict__ nmodes, double u,
                                     int ntrees, ProbOut* __restrict__ po) {
@@ -329,21 +358,57 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
   // requests whose earlier rungs bound |p| away from zero well enough to
   // predict its estimate (FP64's scaled by 2^-55) within rel_tol with a factor
   // 2 of margin; without such a bound a miss would cost ~0.7 of FX on top.
+  // Trees of kSkip64 or more modes skip FP64 unless the a-priori cancellation
+  // estimate (kappa_estimate_kernel) leaves it within kPairReach of rel_tol:
+  // there FP64 almost never certifies and costs ~0.2 of FX for nothing.  The
+  // estimate is exact for independent modes but runs up to 17 orders of
+  // magnitude high on correlated ones, so smaller trees keep the FP64 rung
+  // (cheap, and the bound on |p| it gives admits them to the narrow fixed
+  // point); a tree that skipped FP64 goes to the narrow fixed point only when
+  // the estimate itself predicts success.
   constexpr double kPairReach = 1e3;
+  constexpr int kSkip64 = 16;
   const int ladder[6] = {GBS_PREC_FP64, GBS_PREC_FP64P, GBS_PREC_FXN, GBS_PREC_FX, GBS_PREC_FXW, GBS_PREC_TD};
   const int steps = prec == GBS_PREC_AUTO ? 6 : 1;
   bool uncertified = false;
   std::vector<double> err64(nreq, INFINITY), p_low(nreq, 0.0);  // FP64 estimate, lower bound on |p|
+  std::vector<double> lk(nreq, INFINITY);  // log10 of the a-priori cancellation estimate
+  if (prec == GBS_PREC_AUTO && !todo.empty()) {
+    std::vector<BatchTree> tt(todo.size());
+    for (size_t i = 0; i < todo.size(); ++i) tt[i] = trees[todo[i]];
+    std::vector<double> est(todo.size(), 0.0);
+    const void *d_tt = nullptr, *d_est = nullptr;
+    if ((st = stage(ctx, tt.data(), tt.size() * sizeof(BatchTree), &d_tt)) ||
+        (st = stage(ctx, est.data(), est.size() * sizeof(double), &d_est)))
+      return st;
+    kappa_estimate_kernel<<<(unsigned)((todo.size() + 127) / 128), 128, 0, ctx->stream>>>(
+        (const BatchTree*)d_tt, (int)todo.size(), ctx->hbuf.ptr, real ? 1 : 0, (double*)d_est);
+    count_launch(ctx);
+    if ((st = check_cuda(ctx, cudaMemcpyAsync(est.data(), d_est, est.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                              ctx->stream),
+                         "kappa estimate")) ||
+        (st = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync")))
+      return st;
+    for (size_t i = 0; i < todo.size(); ++i) lk[todo[i]] = est[i];
+  }
+  std::vector<char> ran64(nreq, 0);
   for (int k = 0; k < steps && !todo.empty(); ++k) {
     const int pr = prec == GBS_PREC_AUTO ? ladder[k] : prec;
     std::vector<int> run, next;
     for (int i : todo) {
-      if (prec == GBS_PREC_AUTO && pr == GBS_PREC_FP64P &&
-          !(real && out[i].err_bound <= kPairReach * tol * fabs(out[i].p_hi))) {
+      const double l4n = std::log10(4.0 * std::max(N[i], 1));
+      if (prec == GBS_PREC_AUTO && pr == GBS_PREC_FP64 && N[i] >= kSkip64 &&
+          !(l4n - 53.0 * std::log10(2.0) + lk[i] <= std::log10(kPairReach * tol))) {
         next.push_back(i);
         continue;
       }
-      if (prec == GBS_PREC_AUTO && pr == GBS_PREC_FXN && !(2.0 * err64[i] * 0x1p-55 <= tol * p_low[i])) {
+      if (prec == GBS_PREC_AUTO && pr == GBS_PREC_FP64P &&
+          !(real && ran64[i] && out[i].err_bound <= kPairReach * tol * fabs(out[i].p_hi))) {
+        next.push_back(i);
+        continue;
+      }
+      if (prec == GBS_PREC_AUTO && pr == GBS_PREC_FXN && !(2.0 * err64[i] * 0x1p-55 <= tol * p_low[i]) &&
+          !(std::log10(2.0) + l4n - 108.0 * std::log10(2.0) + lk[i] <= std::log10(tol))) {
         next.push_back(i);
         continue;
       }
@@ -368,7 +433,10 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
     for (size_t i = 0; i < run.size(); ++i) {
       fill(&out[run[i]], res[i], pr, real, ld[i]);
       if (prec != GBS_PREC_AUTO) continue;
-      if (pr == GBS_PREC_FP64) err64[run[i]] = res[i].err;
+      if (pr == GBS_PREC_FP64) {
+        err64[run[i]] = res[i].err;
+        ran64[run[i]] = 1;
+      }
       if (res[i].status == 0) p_low[run[i]] = std::max(p_low[run[i]], fabs(res[i].p_hi) - res[i].err);
       const bool missed = res[i].status == 0 && !(res[i].err <= tol * fabs(res[i].p_hi));
       // triple-double (u = 2^-152) cannot improve on a wide fixed-point result

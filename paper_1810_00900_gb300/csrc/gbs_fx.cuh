@@ -50,10 +50,8 @@ typedef fxn<8, 6> fxws;  // FXW s and sums
 // chain; nothing else in these functions touches it.
 #ifdef __CUDA_ARCH__
 #define GBS_ASM1(op, r, a, b) asm volatile(op " %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b))
-#define GBS_ASM2(op, r, a, b, c) asm volatile(op " %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c))
 #else
 #define GBS_ASM1(op, r, a, b) (r = 0u)
-#define GBS_ASM2(op, r, a, b, c) (r = 0u)
 #endif
 GBS_HD uint32_t add_cc(uint32_t a, uint32_t b) { uint32_t r; GBS_ASM1("add.cc.u32", r, a, b); return r; }
 GBS_HD uint32_t addc_cc(uint32_t a, uint32_t b) { uint32_t r; GBS_ASM1("addc.cc.u32", r, a, b); return r; }
@@ -61,12 +59,7 @@ GBS_HD uint32_t addc(uint32_t a, uint32_t b) { uint32_t r; GBS_ASM1("addc.u32", 
 GBS_HD uint32_t sub_cc(uint32_t a, uint32_t b) { uint32_t r; GBS_ASM1("sub.cc.u32", r, a, b); return r; }
 GBS_HD uint32_t subc_cc(uint32_t a, uint32_t b) { uint32_t r; GBS_ASM1("subc.cc.u32", r, a, b); return r; }
 GBS_HD uint32_t subc(uint32_t a, uint32_t b) { uint32_t r; GBS_ASM1("subc.u32", r, a, b); return r; }
-GBS_HD uint32_t mad_lo_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; GBS_ASM2("mad.lo.cc.u32", r, a, b, c); return r; }
-GBS_HD uint32_t madc_lo_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; GBS_ASM2("madc.lo.cc.u32", r, a, b, c); return r; }
-GBS_HD uint32_t mad_hi_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; GBS_ASM2("mad.hi.cc.u32", r, a, b, c); return r; }
-GBS_HD uint32_t madc_hi_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; GBS_ASM2("madc.hi.cc.u32", r, a, b, c); return r; }
 #undef GBS_ASM1
-#undef GBS_ASM2
 
 // ---------------------------------------------------------------- basics --
 template <int L, int F>
@@ -254,53 +247,39 @@ template <> constexpr int bad_status<fxw>() { return kStatusRange; }
 
 // a * b where b >= 0 has nonzero limbs only in [JLO, JHI] (and, when ILO/IHI
 // are given, a >= 0 only in [ILO, IHI]), for the inverse square root's short
-// operands: low and high halves of the partial products a_i b_j that reach
-// the window (low halves from column F, high halves from column F - 1) are
-// summed in two carry-chained arrays, in either of which the carry out of row
-// i lands in column i + JHI + 1, which no earlier row reached; then the one
-// correction a negative a needs.  At most 2L units of the last place, toward
-// -inf.
+// operands: the general product's rows and guard column restricted to those
+// rows and columns (the carry of row i still lands in column i + JHI + 1, which
+// no earlier row reached), then the one correction a negative a needs.
 template <int JLO, int JHI, int L, int F, int ILO = 0, int IHI = L - 1>
 __device__ __forceinline__ fxn<L, F> mul_short(const fxn<L, F>& a, const fxn<L, F>& b) {
-  constexpr int W = L, C0 = F;
-  uint32_t lo[W], hi[W];
+  constexpr int W = L, G = F - 1;
+  uint32_t r[W + 1];
 #pragma unroll
-  for (int k = 0; k < W; ++k) lo[k] = hi[k] = 0u;
+  for (int k = 0; k <= W; ++k) r[k] = 0u;
 #pragma unroll
   for (int i = ILO; i <= IHI; ++i) {
-    {
-      const int j0 = (C0 - i) > JLO ? (C0 - i) : JLO;
-      const int j1 = (C0 + W - 1 - i) < JHI ? (C0 + W - 1 - i) : JHI;
-      if (j0 <= j1) {
-        lo[i + j0 - C0] = mad_lo_cc(a.w[i], b.w[j0], lo[i + j0 - C0]);
+    const int j0 = (G - i) > JLO ? (G - i) : JLO;
+    const int j1 = (G + W - i) < JHI ? (G + W - i) : JHI;
+    if (j0 > j1) continue;
+    uint32_t carry = 0u;
 #pragma unroll
-        for (int j = j0 + 1; j <= j1; ++j) lo[i + j - C0] = madc_lo_cc(a.w[i], b.w[j], lo[i + j - C0]);
-        if (i + j1 + 1 - C0 < W) lo[i + j1 + 1 - C0] = addc(0u, 0u);
-      }
+    for (int j = j0; j <= j1; ++j) {
+      const unsigned long long t = (unsigned long long)a.w[i] * b.w[j] + r[i + j - G] + carry;
+      r[i + j - G] = (uint32_t)t;
+      carry = (uint32_t)(t >> 32);
     }
-    {
-      const int j0 = (C0 - 1 - i) > JLO ? (C0 - 1 - i) : JLO;
-      const int j1 = (C0 + W - 2 - i) < JHI ? (C0 + W - 2 - i) : JHI;
-      if (j0 <= j1) {
-        hi[i + j0 + 1 - C0] = mad_hi_cc(a.w[i], b.w[j0], hi[i + j0 + 1 - C0]);
-#pragma unroll
-        for (int j = j0 + 1; j <= j1; ++j) hi[i + j + 1 - C0] = madc_hi_cc(a.w[i], b.w[j], hi[i + j + 1 - C0]);
-        if (i + j1 + 2 - C0 < W) hi[i + j1 + 2 - C0] = addc(0u, 0u);
-      }
-    }
+    if (i + j1 + 1 - G <= W) r[i + j1 + 1 - G] = carry;
   }
-  fxn<L, F> r;
-  r.w[0] = add_cc(lo[0], hi[0]);
+  fxn<L, F> out;
 #pragma unroll
-  for (int k = 1; k < L - 1; ++k) r.w[k] = addc_cc(lo[k], hi[k]);
-  r.w[L - 1] = addc(lo[L - 1], hi[L - 1]);
+  for (int k = 0; k < L; ++k) out.w[k] = r[k + 1];
   constexpr int S = L - F;
   const uint32_t ma = (uint32_t)((int32_t)a.w[L - 1] >> 31);
-  r.w[S] = sub_cc(r.w[S], b.w[0] & ma);
+  out.w[S] = sub_cc(out.w[S], b.w[0] & ma);
 #pragma unroll
-  for (int k = S + 1; k < L - 1; ++k) r.w[k] = subc_cc(r.w[k], b.w[k - S] & ma);
-  r.w[L - 1] = subc(r.w[L - 1], b.w[L - 1 - S] & ma);
-  return r;
+  for (int k = S + 1; k < L - 1; ++k) out.w[k] = subc_cc(out.w[k], b.w[k - S] & ma);
+  out.w[L - 1] = subc(out.w[L - 1], b.w[L - 1 - S] & ma);
+  return out;
 }
 
 // 1/sqrt(x) for x in [2^-20, 2^12).  Seed y0: FP64 inverse square root of the
