@@ -24,7 +24,7 @@ gbs_status check_cuda(gbs_ctx* ctx, cudaError_t e, const char* what) {
   return set_error(ctx, GBS_ECUDA, buf);
 }
 
-// Give every cached block back to the driver (they leave in_use with it).
+// Give every cached block back to CUDA (cudaFree; they leave in_use with it).
 void cache_release(gbs_ctx* ctx) {
   std::lock_guard<std::mutex> g(ctx->cache_mu);
   for (auto& kv : ctx->cache) {
@@ -57,7 +57,7 @@ gbs_status dev_alloc(gbs_ctx* ctx, DevBuf& b, size_t bytes) {
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    cache_release(ctx);  // the driver may have been short of memory held in the cache
+    cache_release(ctx);  // CUDA may have been short of memory held in the cache
     e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();

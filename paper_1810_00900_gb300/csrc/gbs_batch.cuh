@@ -105,13 +105,13 @@ __device__ __forceinline__ void untri(int e, int& a, int& b) {
 // `nodes` nodes with q undecided modes (entry-major: entry e of node t at
 // src[e * nodes + t]) and ssrc their s.  Each level replaces node t by its
 // exclude child 2t and include child 2t + 1; on return src/ssrc point at the
-// last level and nodes/q describe it.  Scratch: pm10, pq00, pq11, pg hold one
+// last level and nodes/q describe it.  Scratch: pm10, pq00, pq11 hold one
 // value per node of the level being split.
 template <class E>
 __device__ __forceinline__ void smem_expand(E*& src, E*& dst, typename scale_of<E>::type*& ssrc,
                                             typename scale_of<E>::type*& sdst, E* pm10,
                                             typename real_of<E>::type* pq00, typename real_of<E>::type* pq11,
-                                            typename real_of<E>::type* pg, int& nodes, int& q, int levels,
+                                            int& nodes, int& q, int levels,
                                             bool& bad) {
   typedef typename real_of<E>::type T;
   typedef typename scale_of<E>::type S;
@@ -125,7 +125,6 @@ __device__ __forceinline__ void smem_expand(E*& src, E*& dst, typename scale_of<
       bad |= !is_pos(det);
       const T g = rsqrt_(det);
       const T inv = g * g;
-      pg[t] = g;
       pq00[t] = p00 * inv;
       pq11[t] = p11 * inv;
       pm10[t] = neg_(scale_(p10, inv));
@@ -234,7 +233,6 @@ __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
     S* sdst = ssrc + ncap;
     T* pq00 = reinterpret_cast<T*>(sdst + ncap);
     T* pq11 = pq00 + ncap;
-    T* pg = pq11 + ncap;
     for (int e = threadIdx.x; e < sym(dq); e += blockDim.x) {
       int a, b;
       untri(e, a, b);
@@ -243,7 +241,7 @@ __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
     if (threadIdx.x == 0) ssrc[0] = s;
     __syncthreads();
     int nodes = 1, q = sg.n - sg.dtop;
-    smem_expand<E>(src, dst, ssrc, sdst, pm10, pq00, pq11, pg, nodes, q, sg.emid, bad);
+    smem_expand<E>(src, dst, ssrc, sdst, pm10, pq00, pq11, nodes, q, sg.emid, bad);
     const long long cnt = 1LL << (sg.dtop + sg.emid);
     const long long first = node << sg.emid;
     for (int i = threadIdx.x; i < sym(2 * q) * nodes; i += blockDim.x) {
@@ -376,7 +374,6 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
   S* sB = sA + nthr;
   T* pq00 = reinterpret_cast<T*>(sB + nthr);
   T* pq11 = pq00 + nthr;
-  T* pg = pq11 + nthr;
   for (long long vb = blockIdx.x; vb < total_blocks; vb += gridDim.x) {
     const SubSeg sg = segs[find_seg(segs, nseg, vb, &SubSeg::block_begin)];
     const long long root = vb - sg.block_begin;
@@ -391,7 +388,7 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
     S* sdst = sB;
     int nodes = 1;
     bool bad = false;
-    smem_expand<E>(src, dst, ssrc, sdst, pm10, pq00, pq11, pg, nodes, q, sg.e_levels, bad);
+    smem_expand<E>(src, dst, ssrc, sdst, pm10, pq00, pq11, nodes, q, sg.e_levels, bad);
     if (bad) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
     Red inc = red_zero<Red>(), exc = red_zero<Red>();
     double asum = 0.0;

@@ -74,7 +74,7 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
     ncap = 1 << emax;
     smem_top = emax == 0 ? (size_t)mid_off * sizeof(E)
                          : (size_t)(mid_off + capA_top + capB_top + ncap) * sizeof(E) +
-                               (size_t)ncap * (2 * sizeof(S) + 3 * sizeof(T));
+                               (size_t)ncap * (2 * sizeof(S) + 2 * sizeof(T));
     if (smem_top <= 200 * 1024 || ecap == 0) {
       for (int t = 0; t < ntrees; ++t) emid[t] = std::min(emid[t], ecap);
       break;
@@ -201,7 +201,7 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
     }
     cudaEventRecord(ctx->leaf_timer.start, s);
   }
-  const size_t smem_sub = (size_t)(capA + capB + nthr) * sizeof(E) + (size_t)nthr * (2 * sizeof(S) + 3 * sizeof(T));
+  const size_t smem_sub = (size_t)(capA + capB + nthr) * sizeof(E) + (size_t)nthr * (2 * sizeof(S) + 2 * sizeof(T));
   for (int qv = QMAX; qv >= 1; --qv) {
     const long long nb = grp_blocks[qv];
     if (nb == 0) continue;

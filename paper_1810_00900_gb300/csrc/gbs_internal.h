@@ -120,7 +120,7 @@ gbs_status check_cuda(gbs_ctx* ctx, cudaError_t e, const char* what);
 gbs_status dev_alloc(gbs_ctx* ctx, DevBuf& b, size_t bytes);
 gbs_status dev_reserve(gbs_ctx* ctx, DevBuf& b, size_t bytes);  // grow-only
 void dev_free(gbs_ctx* ctx, DevBuf& b);
-void cache_release(gbs_ctx* ctx);  // return cached device blocks to the driver
+void cache_release(gbs_ctx* ctx);  // return cached device blocks to CUDA (cudaFree)
 inline void count_launch(gbs_ctx* ctx, long long n = 1) { ctx->launches += n; }
 
 // Staging arena: stage_begin() makes room for `bytes` (synchronising first if it

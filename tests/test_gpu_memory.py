@@ -1,5 +1,5 @@
 """Device memory of a context: the HBM budget is enforced (GBS_ENOMEM, context still usable),
-freed blocks are reused instead of returned to the driver, and cached blocks give way when a
+freed blocks are reused instead of returned to CUDA, and cached blocks give way when a
 new allocation needs the room."""
 import numpy as np
 import pytest
