@@ -283,7 +283,7 @@ __device__ __forceinline__ fxn<L, F> mul_short(const fxn<L, F>& a, const fxn<L, 
 }
 
 // 1/sqrt(x) for x in [2^-20, 2^12).  Seed y0: FP64 inverse square root of the
-// value of the integer limb and the three fraction limbs below it (~53 bits);
+// value of the integer limb and the two fraction limbs below it (~53 bits);
 // y0 lies in (2^-6, 2^10], so its bits sit in limbs F-2 .. F.  Then, with
 // e = 1 - x y0^2 (|e| < 2^-50):
 //   128 and 160 fraction bits: one third-order step y0 (1 + e/2 + 3 e^2 / 8),
@@ -295,8 +295,8 @@ __device__ __forceinline__ fxn<L, F> mul_short(const fxn<L, F>& a, const fxn<L, 
 //   192 fraction bits: two Newton steps y <- y + y (1 - x y^2) / 2.
 template <int L, int F>
 __device__ __forceinline__ fxn<L, F> rsqrt_(const fxn<L, F>& x) {
-  const double xd = ((double)x.w[F] + (double)x.w[F - 1] * 0x1p-32) +
-                    ((double)x.w[F - 2] * 0x1p-64 + (double)x.w[F - 3] * 0x1p-96);
+  const double xd = fma((double)x.w[F - 2], 0x1p-64,
+                        (double)(((unsigned long long)x.w[F] << 32) | x.w[F - 1]) * 0x1p-32);
   const fxn<L, F> y0 = fx_from_double<L, F>(rsqrt(xd));
   fxn<L, F> one;
 #pragma unroll
