@@ -282,42 +282,68 @@ __device__ __forceinline__ fxn<L, F> mul_short(const fxn<L, F>& a, const fxn<L, 
   return out;
 }
 
-// 1/sqrt(x) for x in [2^-20, 2^12).  Seed y0: FP64 inverse square root of the
-// value of the integer limb and the two fraction limbs below it (~53 bits);
-// y0 lies in (2^-6, 2^10], so its bits sit in limbs F-2 .. F.  Then, with
-// e = 1 - x y0^2 (|e| < 2^-50):
-//   128 and 160 fraction bits: one third-order step y0 (1 + e/2 + 3 e^2 / 8),
-//     whose remaining error 5 e^3 / 16 is below 2^-155 relative; e^2 comes
-//     from the double of e (the signed 64-bit integer of limbs F-2, F-3 plus
-//     limb F-4: e to 2^-(32 F - 32), so e^2 to 2^-143 or better), and every
-//     product has y0 as its short factor (y0^2 is exact, so x y0^2 is
-//     truncated once);
-//   192 fraction bits: two Newton steps y <- y + y (1 - x y^2) / 2.
+// The value of a float (exact: 24 significant bits placed in the limbs).
+template <int L, int F>
+__device__ __forceinline__ fxn<L, F> fx_from_float(float v) {
+  const uint32_t bits = __float_as_uint(v);
+  const int e = (int)((bits >> 23) & 0xffu);
+  const uint32_t m = e ? ((bits & 0x7fffffu) | 0x800000u) : 0u;  // no subnormal reaches here
+  const int sh = e - 150 + 32 * F;                              // bit position of m's last bit in X
+  fxn<L, F> r;
+#pragma unroll
+  for (int k = 0; k < L; ++k) {
+    const int s = 32 * k - sh;
+    r.w[k] = s >= 0 ? (s < 32 ? m >> s : 0u) : (s > -32 ? m << (-s) : 0u);
+  }
+  return (bits >> 31) ? -r : r;
+}
+
+// 1/sqrt(x) for x in [2^-20, 2^12), on the integer pipe apart from an FP32
+// seed.  Seed: the single-precision inverse square root of the float of x's
+// two leading limbs (from the integer limb, or from the first fraction limb
+// when x < 1; the limbs left out change x by less than 2^-32 relative), with
+// a relative error below 2^-21; when the seed rounded
+// to 12 significant bits squares exactly to 1/x in single precision it is
+// taken instead, so that exact cases (x = 1, 1/4, 4, ...) stay exact.  The
+// seed lies in (2^-6, 2^11), i.e. in limbs F-1 .. F.  Then two third-order
+// steps y <- y (1 + e/2 + 3 e^2 / 8), e = 1 - x y^2:
+//   1. y0^2 is exact (48 bits), e^2 comes from the float of e (|e| < 2^-20);
+//      the result, cut to limbs F-2 .. F (2^-64 resolution), has |e| < 2^-55;
+//   2. y1^2 is exact (192 bits), e^2 is a short product of |e| cut to limbs
+//      F-5 .. F-2; the remaining error 5|e|^3/16 is below 2^-165 relative.
+// Every product has a short nonnegative factor (mul_short).
 template <int L, int F>
 __device__ __forceinline__ fxn<L, F> rsqrt_(const fxn<L, F>& x) {
-  const double xd = fma((double)x.w[F - 2], 0x1p-64,
-                        (double)(((unsigned long long)x.w[F] << 32) | x.w[F - 1]) * 0x1p-32);
-  const fxn<L, F> y0 = fx_from_double<L, F>(rsqrt(xd));
   fxn<L, F> one;
 #pragma unroll
   for (int k = 0; k < L; ++k) one.w[k] = k == F ? 1u : 0u;
-  if constexpr (F <= 5) {
-    // y0^2 has ~106 bits, all above 2^-117: exact in the window
-    const fxn<L, F> y2 = mul_short<F - 2, F, L, F, F - 2, F>(y0, y0);
-    const fxn<L, F> e = one - mul_short<F - 4, F>(x, y2);
-    const long long e96 = (long long)(((unsigned long long)e.w[F - 2] << 32) | e.w[F - 3]);
-    const double ed = fma((double)e.w[F - 4], 0x1p-128, (double)e96 * 0x1p-96);
-    const fxn<L, F> c = fx_half(e) + fx_from_double<L, F>(0.375 * ed * ed);
-    return y0 + mul_short<F - 2, F>(c, y0);
-  } else {
-    fxn<L, F> y = y0;
+  const float xf = x.w[F] ? __ull2float_rn(((unsigned long long)x.w[F] << 32) | x.w[F - 1]) * 0x1p-32f
+                          : __ull2float_rn(((unsigned long long)x.w[F - 1] << 32) | x.w[F - 2]) * 0x1p-64f;
+  float yf = rsqrtf(xf);
+  const float ys = __uint_as_float((__float_as_uint(yf) + 0x800u) & ~0xfffu);
+  if (fmaf(xf * ys, ys, -1.0f) == 0.0f) yf = ys;
+  const fxn<L, F> y0 = fx_from_float<L, F>(yf);
+  // step 1
+  const fxn<L, F> y0sq = mul_short<F - 1, F, L, F, F - 1, F>(y0, y0);
+  const fxn<L, F> e0 = one - mul_short<F - 2, F>(x, y0sq);
+  const float e0f = __ll2float_rn((long long)(((unsigned long long)e0.w[F - 1] << 32) | e0.w[F - 2])) * 0x1p-64f;
+  const fxn<L, F> c0 = fx_half(e0) + fx_from_float<L, F>(0.375f * e0f * e0f);
+  fxn<L, F> y1 = y0 + mul_short<F - 1, F>(c0, y0);
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      const fxn<L, F> e = one - x * (y * y);
-      y = y + fx_half(y * e);
-    }
-    return y;
-  }
+  for (int k = 0; k < F - 2; ++k) y1.w[k] = 0u;
+  // step 2
+  constexpr int ELO = F - 5 > 0 ? F - 5 : 0;
+  const fxn<L, F> y1sq = mul_short<F - 2, F, L, F, F - 2, F>(y1, y1);
+  const fxn<L, F> e1 = one - mul_short<F - 4, F>(x, y1sq);
+  const bool neg = (int32_t)e1.w[L - 1] < 0;
+  fxn<L, F> ae = neg ? -e1 : e1;
+#pragma unroll
+  for (int k = 0; k < L; ++k)
+    if (k < ELO || k > F - 2) ae.w[k] = 0u;
+  const fxn<L, F> esq = mul_short<ELO, F - 2, L, F, ELO, F - 2>(ae, ae);
+  const fxn<L, F> q = fx_half(fx_half(esq));
+  const fxn<L, F> c1 = fx_half(e1) + (q + fx_half(q));  // e/2 + 3 e^2 / 8
+  return y1 + mul_short<F - 2, F>(c1, y1);
 }
 
 // ------------------------------------------------------ sums and reduction --
