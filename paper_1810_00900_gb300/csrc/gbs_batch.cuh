@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256, level_min_blocks<E>::value) batch_level_k
 
 // ----------------------------------------------------------------- leaf --
 template <class E, int Q, bool PAIR = false>
-__global__ void __launch_bounds__(128) batch_leaf_kernel(const LeafSeg* __restrict__ segs, int nseg,
+__global__ void __launch_bounds__(128, leaf_min_blocks<E>::value) batch_leaf_kernel(const LeafSeg* __restrict__ segs, int nseg,
                                                          long long total_blocks, const E* __restrict__ buf0,
                                                          const E* __restrict__ buf1,
                                                          const typename scale_of<E>::type* __restrict__ s0,

@@ -242,6 +242,7 @@ template <> struct level_min_blocks<fxn4> { static const int value = 3; };
 template <> constexpr int bad_status<fx>() { return kStatusRange; }
 template <> struct level_min_blocks<fx> { static const int value = 3; };
 template <int L, int F> struct node_words<fxn<L, F>> { static const int value = L; };
+template <int L, int F> struct leaf_min_blocks<fxn<L, F>> { static const int value = 4; };
 template <> struct level_min_blocks<fxw> { static const int value = 3; };
 template <> constexpr int bad_status<fxw>() { return kStatusRange; }
 

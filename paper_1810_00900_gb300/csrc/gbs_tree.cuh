@@ -67,6 +67,8 @@ template <class E> struct scale_of { typedef typename real_of<E>::type type; };
 // breadth-first level kernel: the fixed-point levels wait on global loads with
 // too few warps otherwise.
 template <class E> struct level_min_blocks { static const int value = 1; };
+// The same for the register-subtree leaf kernel (128-thread CTAs).
+template <class E> struct leaf_min_blocks { static const int value = 1; };
 
 // 32-bit words of a multiword entry stored limb by limb in the global node
 // buffers of the batched engine (0: the entry is stored whole).
