@@ -169,7 +169,8 @@ def single_large_torontonian_workload(N: int = 24):
 
 
 # Mode counts of the paper's walltime benchmark (Table II): l modes for m clicks.
-WALLTIME_MODES = {10: 200, 12: 288, 14: 392, 16: 512, 18: 624, 20: 800}
+# the paper's Table II sizes, then two rows past its largest one with l = 2 m^2
+WALLTIME_MODES = {10: 200, 12: 288, 14: 392, 16: 512, 18: 624, 20: 800, 22: 968, 24: 1152}
 
 
 def walltime_workload(m: int, seed: int = 10):
