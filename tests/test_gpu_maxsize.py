@@ -71,3 +71,20 @@ def test_n24_lossy_wide_fixed_point_and_fp64_agree_on_abs(ctx):
     assert abs(pw.abs_sum / p64.abs_sum - 1.0) < 1e-12
     assert abs(pw.tor_value - pf.tor_value) <= 1e-12 * abs(pw.tor_value)
     st.free()
+
+
+def test_auto_skips_fp64_for_large_trees_and_predicts_the_narrow_width(ctx):
+    # 18 independent modes, kappa = prod (sqrt(d)+1)/(sqrt(d)-1) ~ 1e12 (the a-priori estimate is
+    # exact for independent modes): FP64 cannot reach 1e-10 and a tree of 16+ modes skips it; the
+    # estimate predicts the 128-bit fixed point suffices
+    r = np.concatenate([np.full(18, 1.0), np.full(4, 0.5)])
+    st_p = gi.identity_state(r, 1.0)
+    st = gbs.build_state(ctx, st_p.U, st_p.r, 1.0)
+    modes = np.arange(18)
+    want, kappa = closed_form(r, 1.0, modes)
+    assert 1e11 < kappa < 1e13
+    pr = gbs.torontonian(ctx, st, modes, "auto", "real")
+    assert pr.prec == "fxn"
+    assert abs(pr.tor_value - want) <= 1e-12 * abs(want)
+    assert pr.err_bound <= 1e-10 * abs(pr.p)
+    st.free()
