@@ -373,7 +373,9 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
   bool uncertified = false;
   std::vector<double> err64(nreq, INFINITY), p_low(nreq, 0.0);  // FP64 estimate, lower bound on |p|
   std::vector<double> lk(nreq, INFINITY);  // log10 of the a-priori cancellation estimate
-  if (prec == GBS_PREC_AUTO && !todo.empty()) {
+  bool need_estimate = false;  // only trees that may skip FP64 use it
+  for (int i : todo) need_estimate |= N[i] >= kSkip64;
+  if (prec == GBS_PREC_AUTO && need_estimate) {
     std::vector<BatchTree> tt(todo.size());
     for (size_t i = 0; i < todo.size(); ++i) tt[i] = trees[todo[i]];
     std::vector<double> est(todo.size(), 0.0);
