@@ -374,12 +374,15 @@ gbs_status gbs_subset_sum(gbs_ctx* ctx, int n, const double* G, int basis, int p
  *           definite (then the sums are meaningless);
  *   cuda_stream  the cudaStream_t the work is queued on (0 = legacy default).
  * The call is asynchronous: it returns after queueing (GBS_OK), GBS_EINVAL or
- * GBS_ECUDA (a launch failed, or the device array could not be located).
+ * GBS_ECUDA (one of its launches failed, or the device array could not be
+ * located).  A CUDA error that earlier work left pending is reported as
+ * GBS_ECUDA before anything is queued, and is not cleared.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the one array and each leaves
- * its data there: calls that can overlap on the GPU race and must be ordered
- * by the caller (one stream, or events). */
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the life
+ * of the process; make that first call before any stream capture, and do not
+ * call this entry point on a device after a cudaDeviceReset of it.  All calls
+ * share the one array and each leaves its data there: calls that can overlap
+ * on the GPU race and must be ordered by the caller (one stream, or events). */
 gbs_status gbs_subset_sum_static(const double* G_dev, int n, double* out_dev, void* cuda_stream);
 
 #ifdef __cplusplus

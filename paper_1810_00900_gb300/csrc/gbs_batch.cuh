@@ -122,7 +122,7 @@ __device__ __forceinline__ void smem_expand(E*& src, E*& dst, typename scale_of<
       const T p11 = re_of(src[tri(1, 1) * nodes + t]);
       const E p10 = src[tri(1, 0) * nodes + t];
       const T det = p00 * p11 - norm2(p10);
-      bad |= !is_pos(det);
+      bad |= !is_pos(det) || !lead_pos(p00);
       const T g = rsqrt_(det);
       const T inv = g * g;
       pq00[t] = p00 * inv;
@@ -184,7 +184,7 @@ __global__ void batch_top_kernel(const TopSeg* __restrict__ segs, int nseg,
     const T p00 = re_of(C[tri(o, o)]), p11 = re_of(C[tri(o + 1, o + 1)]);
     const E p10 = C[tri(o + 1, o)];
     const T det = p00 * p11 - norm2(p10);
-    bad |= !is_pos(det);
+    bad |= !is_pos(det) || !lead_pos(p00);
     const T g = rsqrt_(det);
     const T inv = g * g;
     const T q00 = p00 * inv, q11 = p11 * inv;
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256, level_min_blocks<E>::value) batch_level_k
   const T p11 = re_of(PAR(1, 1));
   const E p10 = PAR(1, 0);
   const T det = p00 * p11 - norm2(p10);
-  if (!is_pos(det)) {
+  if (!is_pos(det) || !lead_pos(p00)) {
     if (grp == 0) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
     return;
   }

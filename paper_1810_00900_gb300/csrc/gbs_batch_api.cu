@@ -365,7 +365,9 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
   // magnitude high on correlated ones, so smaller trees keep the FP64 rung
   // (cheap, and the bound on |p| it gives admits them to the narrow fixed
   // point); a tree that skipped FP64 goes to the narrow fixed point only when
-  // the estimate itself predicts success.
+  // the estimate itself predicts success.  Only trees of kSkip64 or more modes
+  // consult the estimate, so it is computed only when the batch holds one, and
+  // a request's rungs never depend on what it is batched with.
   constexpr double kPairReach = 1e3;
   constexpr int kSkip64 = 16;
   const int ladder[6] = {GBS_PREC_FP64, GBS_PREC_FP64P, GBS_PREC_FXN, GBS_PREC_FX, GBS_PREC_FXW, GBS_PREC_TD};
@@ -373,7 +375,7 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
   bool uncertified = false;
   std::vector<double> err64(nreq, INFINITY), p_low(nreq, 0.0);  // FP64 estimate, lower bound on |p|
   std::vector<double> lk(nreq, INFINITY);  // log10 of the a-priori cancellation estimate
-  bool need_estimate = false;  // only trees that may skip FP64 use it
+  bool need_estimate = false;  // only trees of kSkip64+ modes use it (to skip FP64, and then for FXN)
   for (int i : todo) need_estimate |= N[i] >= kSkip64;
   if (prec == GBS_PREC_AUTO && need_estimate) {
     std::vector<BatchTree> tt(todo.size());
@@ -410,7 +412,7 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
         continue;
       }
       if (prec == GBS_PREC_AUTO && pr == GBS_PREC_FXN && !(2.0 * err64[i] * 0x1p-55 <= tol * p_low[i]) &&
-          !(std::log10(2.0) + l4n - 108.0 * std::log10(2.0) + lk[i] <= std::log10(tol))) {
+          !(N[i] >= kSkip64 && std::log10(2.0) + l4n - 108.0 * std::log10(2.0) + lk[i] <= std::log10(tol))) {
         next.push_back(i);
         continue;
       }

@@ -237,6 +237,8 @@ GBS_HD bool fx_det_in_range(const fxn<L, F>& d) {
 }
 template <int L, int F> GBS_HD bool not_positive(const fxn<L, F>& d) { return !fx_det_in_range(d); }
 template <int L, int F> GBS_HD bool is_pos(const fxn<L, F>& d) { return fx_det_in_range(d); }
+// Fixed-point trees run only on matrices the host has bounded (positive definite).
+template <int L, int F> GBS_HD bool lead_pos(const fxn<L, F>&) { return true; }
 template <> constexpr int bad_status<fxn4>() { return kStatusRange; }
 template <> struct level_min_blocks<fxn4> { static const int value = 3; };
 template <> constexpr int bad_status<fx>() { return kStatusRange; }

@@ -15,7 +15,9 @@
 // The array is shared by every call: calls whose work overlaps on the GPU (on
 // different streams without ordering between them) race on it.  Each call
 // clears the status word it reads; everything else it reads was written by the
-// same call.
+// same call.  The array's device address is looked up once per device (first
+// call on it) and kept for the life of the process, so the entry point must not
+// be used on a device after cudaDeviceReset of that device in the same process.
 #include <mutex>
 
 #include "gbs_internal.h"
@@ -112,8 +114,17 @@ __global__ void static_emit_kernel(const TreeOut* __restrict__ t, const int* __r
 
 using namespace gbs;
 
+// Errors of this call's own launches are read right after each launch; an
+// error that earlier work left pending is found before anything is queued and
+// reported as GBS_ECUDA without being cleared.
+#define GBS_STATIC_LAUNCHED()                               \
+  do {                                                      \
+    if (cudaGetLastError() != cudaSuccess) return GBS_ECUDA; \
+  } while (0)
+
 extern "C" gbs_status gbs_subset_sum_static(const double* G_dev, int n, double* out_dev, void* cuda_stream) {
   if (n < 1 || n > kStaticMaxN || !G_dev || !out_dev) return GBS_EINVAL;
+  if (cudaPeekAtLastError() != cudaSuccess) return GBS_ECUDA;
   unsigned char* base = nullptr;
   if (scratch_address((void**)&base) != cudaSuccess) return GBS_ECUDA;
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -129,6 +140,7 @@ extern "C" gbs_status gbs_subset_sum_static(const double* G_dev, int n, double* 
   const int blocks = (int)((leaves + 127) / 128);
   const int nent = sym(2 * n);
   static_pack_kernel<<<(nent + 255) / 256, 256, 0, s>>>(G_dev, n, lv[0], sv[0], status);
+  GBS_STATIC_LAUNCHED();
   int cur = 0;
   for (int l = 0; l < depth; ++l) {
     const long long count = 1LL << l;
@@ -136,6 +148,7 @@ extern "C" gbs_status gbs_subset_sum_static(const double* G_dev, int n, double* 
     const long long threads = count * (2 * q - 2);
     tree_level_kernel<double><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(lv[cur], sv[cur], count, q,
                                                                                lv[cur ^ 1], sv[cur ^ 1], status);
+    GBS_STATIC_LAUNCHED();
     cur ^= 1;
   }
   switch (Q) {
@@ -145,7 +158,11 @@ extern "C" gbs_status gbs_subset_sum_static(const double* G_dev, int n, double* 
     case 4: tree_leaf_kernel<double, 4><<<blocks, 128, 0, s>>>(lv[cur], sv[cur], leaves, depth, parts, status); break;
     default: tree_leaf_kernel<double, 5><<<blocks, 128, 0, s>>>(lv[cur], sv[cur], leaves, depth, parts, status); break;
   }
+  GBS_STATIC_LAUNCHED();
   tree_final_kernel<dd><<<1, 256, 0, s>>>(parts, blocks, tout);
+  GBS_STATIC_LAUNCHED();
   static_emit_kernel<<<1, 32, 0, s>>>(tout, status, out_dev);
-  return cudaGetLastError() == cudaSuccess ? GBS_OK : GBS_ECUDA;
+  GBS_STATIC_LAUNCHED();
+  return GBS_OK;
 }
+#undef GBS_STATIC_LAUNCHED

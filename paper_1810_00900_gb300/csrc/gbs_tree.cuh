@@ -155,6 +155,12 @@ GBS_HD bool is_pos(double x) { return x > 0.0; }
 GBS_HD bool is_pos(float x) { return x > 0.0f; }
 GBS_HD bool is_pos(const dd& x) { return x.hi > 0.0; }
 GBS_HD bool is_pos(const td& x) { return x.x0 > 0.0; }
+// The first diagonal entry of a pivot block is positive: with det > 0 the 2 x 2
+// block is then positive definite (det > 0 alone admits a negative definite one).
+GBS_HD bool lead_pos(double x) { return x > 0.0; }
+GBS_HD bool lead_pos(float x) { return x > 0.0f; }
+GBS_HD bool lead_pos(const dd& x) { return x.hi > 0.0; }
+GBS_HD bool lead_pos(const td& x) { return x.x0 > 0.0; }
 
 // --------------------------------------------------- breadth-first level --
 // Parents: count nodes with q undecided modes, entry e of node i at par[e*count + i].
@@ -177,7 +183,7 @@ __global__ void tree_level_kernel(const E* __restrict__ par, const typename scal
   const T p11 = re_of(PAR(1, 1));
   const E p10 = PAR(1, 0);
   const T det = p00 * p11 - norm2(p10);
-  if (!(to_double(det) > 0.0)) {
+  if (!(to_double(det) > 0.0) || !(to_double(p00) > 0.0)) {
     if (a == 0) atomicExch(status, (int)kStatusNotPD);
     return;
   }
@@ -247,7 +253,7 @@ __device__ __forceinline__ void pair_group(const double (&c)[sym(D)], double s, 
   const double u00 = c[tri(OFF + 2, OFF)], u01 = c[tri(OFF + 2, OFF + 1)];
   const double u10 = c[tri(OFF + 3, OFF)], u11 = c[tri(OFF + 3, OFF + 1)];
   const double da = fma(a00, a11, -a01 * a01);
-  const double ga = rsqrt(da);
+  const double ga = rsqrt_f64(da);
   const double inv = ga * ga;
   const double q00 = a00 * inv, q11 = a11 * inv, m = -a01 * inv;
   // rows of B P_a^-1, then D = B P_a^-1 B^T
@@ -259,7 +265,7 @@ __device__ __forceinline__ void pair_group(const double (&c)[sym(D)], double s, 
   const double c00 = b00 - d00, c11 = b11 - d11, c01 = b01 - d01;
   const double db = fma(b00, b11, -b01 * b01);
   const double dc = fma(c00, c11, -c01 * c01);
-  const double gb = rsqrt(db), gc = rsqrt(dc);
+  const double gb = rsqrt_f64(db), gc = rsqrt_f64(dc);
   const double ha = pair_hm1(a00, a11, a01, da, ga);
   const double hc = pair_hm1(c00, c11, c01, dc, gc);
   const double delta = fma(d00, d11, -d01 * d01) - fma(b11, d00, fma(b00, d11, -2.0 * b01 * d01));
@@ -279,7 +285,7 @@ template <int D, int OFF, bool NEG>
 __device__ __forceinline__ void pair_single(const double (&c)[sym(D)], double s, Sums<double>& acc) {
   const double p00 = c[tri(OFF, OFF)], p11 = c[tri(OFF + 1, OFF + 1)], p01 = c[tri(OFF + 1, OFF)];
   const double det = fma(p00, p11, -p01 * p01);
-  const double g = rsqrt(det);
+  const double g = rsqrt_f64(det);
   const double h = pair_hm1(p00, p11, p01, det, g);
   if (NEG) acc.ip = fma(-s, h, acc.ip); else acc.ip = fma(s, h, acc.ip);
   acc.ep = fma(s, fabs(h) + g, acc.ep);
@@ -298,6 +304,41 @@ struct Dfs {
     if constexpr (PAIR && Q <= 2) {
       static_assert(std::is_same<E, double>::value, "the paired last levels are FP64 real-basis only");
       if constexpr (Q == 2) pair_group<D, OFF, NEG>(c, s, acc); else pair_single<D, OFF, NEG>(c, s, acc);
+    } else if constexpr (std::is_same<E, double>::value) {
+      // FP64 real basis, the pivot block factored as P = R R^T (Cholesky):
+      //   r0 = p00^(-1/2), w = p10 r0, d1 = p11 - w^2, r1 = d1^(-1/2),
+      //   det(P)^(-1/2) = r0 r1,
+      // and the rank-2 update as C' = C - W W^T with the rows of W = U R^-T:
+      //   w0 = u0 r0,  w1 = (u1 - w0 w) r1 = u1 r1 + u0 (-w r0 r1),
+      // three FP64 instructions per row where u P^-1 takes four; an entry still
+      // costs two fused multiply-adds.  A one-mode node needs only det(P).
+      const double p00 = c[tri(OFF, OFF)], p11 = c[tri(OFF + 1, OFF + 1)], p10 = c[tri(OFF + 1, OFF)];
+      if constexpr (Q == 1) {
+        const double g = rsqrt_f64(fma(p00, p11, -p10 * p10));
+        if (NEG) { acc.in = fma(s, g, acc.in); acc.ep += s; } else { acc.ip = fma(s, g, acc.ip); acc.en += s; }
+      } else {
+        constexpr int DN = 2 * Q - 2;
+        const double r0 = rsqrt_f64(p00);
+        const double w = p10 * r0;
+        const double r1 = rsqrt_f64(fma(-w, w, p11));
+        const double g = r0 * r1;
+        const double kap = -w * g;
+        double w0[DN], w1[DN];
+#pragma unroll
+        for (int a = 0; a < DN; ++a) {
+          const double u0 = c[tri(OFF + 2 + a, OFF)], u1 = c[tri(OFF + 2 + a, OFF + 1)];
+          w0[a] = u0 * r0;
+          w1[a] = fma(u0, kap, u1 * r1);
+        }
+        double cn[sym(DN)];
+#pragma unroll
+        for (int a = 0; a < DN; ++a)
+#pragma unroll
+          for (int b = 0; b <= a; ++b)
+            cn[tri(a, b)] = fma(-w1[a], w1[b], fma(-w0[a], w0[b], c[tri(OFF + 2 + a, OFF + 2 + b)]));
+        Dfs<E, Q - 1, DN, 0, NEG, PAIR>::run(cn, s * g, acc, bad);
+        Dfs<E, Q - 1, D, OFF + 2, !NEG, PAIR>::run(c, s, acc, bad);
+      }
     } else {
     const T p00 = re_of(c[tri(OFF, OFF)]);
     const T p11 = re_of(c[tri(OFF + 1, OFF + 1)]);

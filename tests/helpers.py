@@ -21,3 +21,24 @@ def td_value(x) -> float:
 def frac3(x):
     from fractions import Fraction
     return Fraction(float(x[0])) + Fraction(float(x[1])) + Fraction(float(x[2]))
+
+
+# Parity references: the oracle's plain definition (O1: every subset by its own
+# LU, ~212-bit) up to BRUTE_N modes, its decision tree (O2) beyond; O2 itself
+# is pinned to O1 up to 16 modes by the CPU tests.
+BRUTE_N = 14
+_TOR_CACHE = {}
+
+
+def ref_method(n: int) -> str:
+    return "bruteforce" if n <= BRUTE_N else "tree"
+
+
+def oracle_tor(G):
+    """(Tor as the oracle's QD value, sum of |terms|) of a 2n x 2n block, cached per matrix."""
+    import oracle
+    G = np.ascontiguousarray(G, dtype=np.complex128)
+    key = (G.shape, G.tobytes())
+    if key not in _TOR_CACHE:
+        _TOR_CACHE[key] = oracle.torontonian(G, ref_method(G.shape[0] // 2))
+    return _TOR_CACHE[key]

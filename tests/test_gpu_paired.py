@@ -13,7 +13,7 @@ import pytest
 import gbs_inputs as gi
 import oracle
 import paper_1810_00900_gb300 as gbs
-from helpers import frac3, real_basis_block
+from helpers import frac3, oracle_tor, real_basis_block
 
 pytestmark = pytest.mark.gpu
 
@@ -38,7 +38,7 @@ def haar_H(N, seed=1, M=200, r=0.8, eta=1.0):
 def paired_error(ctx, H):
     n = H.shape[0] // 2
     G = real_basis_block(H)
-    ref, ref_abs = oracle.torontonian(G.astype(np.complex128))
+    ref, ref_abs = oracle_tor(G)
     inc, exc, tor, a_p = gbs.subset_sum(ctx, G, "real", "fp64p")
     assert frac3(exc) == 0 and frac3(inc) == frac3(tor)
     err = float(abs(frac3(tor) - ref.to_fraction()))
@@ -89,7 +89,7 @@ def test_identity_closed_form(ctx):
 def test_launch_shapes_agree(ctx):
     H = haar_H(13, seed=3)
     G = real_basis_block(H)
-    ref, _ = oracle.torontonian(G.astype(np.complex128))
+    ref, _ = oracle_tor(G)
     saved = ctx.tuning("fp64p", "real")
     vals = []
     try:
@@ -114,7 +114,7 @@ def test_batch_of_uneven_requests(ctx):
     pats = [gi.random_modes(150, n, seed=40 + n) for n in (1, 2, 4, 7, 9, 12)]
     res = gbs.torontonian_batch(ctx, [st] * len(pats), pats, "fp64p", "real")
     for m, pr in zip(pats, res):
-        ref, _ = oracle.torontonian(oracle.sigma_inv_block(Sig, m))
+        ref, _ = oracle_tor(oracle.sigma_inv_block(Sig, m))
         want = float(ref.to_fraction())
         assert abs(pr.tor_value - want) <= pr.err_bound / np.exp(-0.5 * pr.logdet_sigma), (len(m), pr.tor_value, want)
     st.free()
@@ -139,7 +139,7 @@ def test_auto_ladder_uses_the_paired_rung(ctx):
     st = gbs.build_state(ctx, st_p.U, st_p.r, 1.0)
     modes = gi.random_modes(200, 8, seed=1)
     Sig = oracle.sigma(oracle.covariance(st_p.U, st_p.r, 1.0))
-    ref, _ = oracle.torontonian(oracle.sigma_inv_block(Sig, modes))
+    ref, _ = oracle_tor(oracle.sigma_inv_block(Sig, modes))
     want = float(ref.to_fraction())
     pr = gbs.torontonian(ctx, st, modes, "auto", "real", rel_tol=1e-5)
     assert pr.prec == "fp64p"

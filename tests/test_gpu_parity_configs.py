@@ -1,0 +1,157 @@
+"""Parity of the served and batched workloads against the oracle.
+
+* Graph-encoded lossy states, as in the served dense-subgraph stream: a
+  100-vertex Erdos-Renyi graph (p = 0.1) with a planted 20-vertex part
+  (p = 0.9), Takagi-encoded with mean photon number 2N for N = 8 (paper Sec. IV),
+  then transmissivity 0.5 or 0.25.  The no-click probability p0 at every step of
+  a forced trajectory, and seeded free samples postselected on N clicks, are
+  compared with oracle.sample_chain (the Sec. II update rule in closed form);
+  draws with |u - p0| < 1e-9 are near-ties and may differ.
+* Free (unforced) sampling on a 48-mode lossy Haar state: chains of 48 steps
+  through the device coin, early rejection and near-tie counting.
+* One AUTO batch of uneven probability requests from the 4096-request workload
+  that holds its first 400-mode requests of 17, 20 and 22 clicks next to smaller
+  ones; the large ones against the oracle values stored in
+  tests/golden/batched_m400.txt (written by tests/golden/make_golden.py), the
+  small ones against the oracle's brute-force definition, all at 1e-9.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import gbs_inputs as gi
+import oracle
+import paper_1810_00900_gb300 as gbs
+from helpers import ref_method
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1810_00900_gb300 import build
+    build.build()
+    c = gbs.Context(0)
+    yield c
+    c.close()
+
+
+def graph_case(ctx, eta, N=8):
+    A = gi.planted_graph(100, 11)
+    sp = gi.graph_state(A, 2.0 * N, eta)
+    st = gbs.build_state(ctx, sp.U, sp.r, sp.eta)
+    Sig = oracle.sigma(oracle.covariance(sp.U, sp.r, sp.eta))
+    return st, Sig
+
+
+@pytest.mark.parametrize("eta", [0.5, 0.25])
+def test_graph_state_forced_trajectory_p0_every_step(ctx, eta):
+    st, Sig = graph_case(ctx, eta)
+    forced = gi.planted_vertices(100, 11)[:8].astype(np.int32)[None, :]
+    pats, p0, stats, status = gbs.sample(ctx, st, 1, seed=4, N_post=8, forced_clicks=forced, want_p0=True)
+    assert status == 0 and stats["uncertified"] == 0
+    ref = oracle.sample_chain(Sig, 4, forced_clicks=forced[0])
+    assert np.array_equal(np.nonzero(pats[0])[0], np.sort(forced[0]))
+    assert np.allclose(p0[0], np.array(ref["p0"]), rtol=0, atol=1e-10), np.max(np.abs(p0[0] - np.array(ref["p0"])))
+    st.free()
+
+
+@pytest.mark.parametrize("eta", [0.5, 0.25])
+def test_graph_state_postselected_free_samples(ctx, eta):
+    st, Sig = graph_case(ctx, eta)
+    n, N_post, attempts = 2, 8, 40
+    pats, p0, stats, status = gbs.sample(ctx, st, n, seed=7, N_post=N_post, max_attempts=attempts, want_p0=True)
+    assert stats["uncertified"] == 0
+    accepted = 0
+    for i in range(n):
+        ref = oracle.sample_chain(Sig, 7, sample=i, N_post=N_post, max_attempts=attempts)
+        if ref["pattern"] is None:
+            assert np.all(pats[i] == 0xFF) or stats["near_ties"] > 0
+            continue
+        if not np.array_equal(pats[i], ref["pattern"]):
+            assert stats["near_ties"] > 0, i  # only a near-tie may change the outcome
+            continue
+        accepted += 1
+        assert pats[i].sum() == N_post
+        assert np.allclose(p0[i], np.array(ref["p0"]), rtol=0, atol=1e-10)
+    assert stats["rejections"] > 0
+    assert accepted >= 1
+
+
+def test_free_sampling_48_modes(ctx):
+    M = 48
+    U = gi.haar_unitary(M, 44)
+    r = gi.uniform_range(44, "squeezing", M, 0.5, 1.0)
+    st = gbs.build_state(ctx, U, r, 0.8)
+    Sig = oracle.sigma(oracle.covariance(U, r, 0.8))
+    n = 8
+    pats, p0, stats, status = gbs.sample(ctx, st, n, seed=123, want_p0=True)
+    assert status == 0 and stats["uncertified"] == 0
+    near = 0
+    clicks = 0
+    for i in range(n):
+        ref = oracle.sample_chain(Sig, 123, sample=i)
+        near += ref["near_ties"]
+        clicks += int(ref["pattern"].sum())
+        if ref["near_ties"] == 0:
+            assert np.array_equal(pats[i], ref["pattern"]), i
+            assert np.allclose(p0[i], np.array(ref["p0"]), rtol=0, atol=1e-10)
+    assert stats["near_ties"] == near
+    assert clicks >= 2 * n  # chains that click: the trees do grow along the way
+    # postselected on 6 clicks: early rejection along 48-step chains
+    n2, N_post, attempts = 4, 6, 30
+    pats2, _, stats2, _ = gbs.sample(ctx, st, n2, seed=321, N_post=N_post, max_attempts=attempts)
+    for i in range(n2):
+        ref = oracle.sample_chain(Sig, 321, sample=i, N_post=N_post, max_attempts=attempts)
+        if ref["pattern"] is None:
+            assert np.all(pats2[i] == 0xFF) or stats2["near_ties"] > 0
+        elif not np.array_equal(pats2[i], ref["pattern"]):
+            assert stats2["near_ties"] > 0, i
+    assert stats2["rejections"] > 0
+    st.free()
+
+
+def stored_batched_m400():
+    rows = []
+    with open(os.path.join(HERE, "golden", "batched_m400.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = line.split()
+            rows.append((int(v[0]), int(v[1]), float(v[4])))
+    return rows
+
+
+def test_batched_workload_with_large_400_mode_requests(ctx):
+    reqs = gi.batched_requests(4096)
+    stored = stored_batched_m400()
+    assert sorted(N for _, N, _ in stored) == [17, 20, 22]
+    big = {i: p for i, _, p in stored}
+    # small neighbours from the same workload (checked against the plain definition)
+    small = [j for j, q in enumerate(reqs[:200]) if q.N <= 10][:9]
+    idx = small[:3] + [stored[0][0]] + small[3:6] + [stored[1][0]] + small[6:] + [stored[2][0]]
+    states, pats = [], []
+    for j in idx:
+        q = reqs[j]
+        states.append(gbs.build_state(ctx, gi.haar_unitary(q.M, q.seed), np.full(q.M, q.r), q.eta))
+        pats.append(q.modes)
+    # AUTO certifies to 1e-10 where its last rung can; a tree whose widest fixed-point bound
+    # stays above that returns GBS_EPRECISION with its value filled in: judged at 1e-9 here
+    res = gbs.torontonian_batch(ctx, states, pats, "auto", "real", check=False)
+    for j, st, pat, pr in zip(idx, states, pats, res):
+        q = reqs[j]
+        if j in big:
+            p_ref = big[j]
+            assert pr.prec != "fp64"  # the cancellation of these trees is far beyond FP64
+        else:
+            p_ref, _, _ = oracle.click_probability(gi.haar_unitary(q.M, q.seed), np.full(q.M, q.r), q.eta, q.modes,
+                                                   method=ref_method(q.N))
+        assert abs(pr.p - p_ref) <= 1e-9 * abs(p_ref), (j, q.M, q.N, pr.p, p_ref, pr.prec)
+        assert pr.err_bound <= 1e-9 * abs(pr.p)
+        if j in big:
+            alone = gbs.torontonian(ctx, st, pat, pr.prec, "real")
+            assert alone.p == pr.p and alone.tor == pr.tor
+    for st in states:
+        st.free()

@@ -15,7 +15,7 @@ import pytest
 import gbs_inputs as gi
 import oracle
 import paper_1810_00900_gb300 as gbs
-from helpers import frac3, real_basis_block
+from helpers import frac3, oracle_tor, real_basis_block
 
 pytestmark = pytest.mark.gpu
 
@@ -48,10 +48,10 @@ def test_every_precision_within_its_bound(ctx, i):
     U, r, eta, modes = case(i)
     st = gbs.build_state(ctx, U, r, eta)
     Sig = oracle.sigma(oracle.covariance(U, r, eta))
-    ref, ref_abs = oracle.torontonian(oracle.sigma_inv_block(Sig, modes))
+    ref, ref_abs = oracle_tor(oracle.sigma_inv_block(Sig, modes))
     want = float(ref.to_fraction())
     G = real_basis_block(oracle.sigma_inv_block(Sig, modes))
-    gref, _ = oracle.torontonian(G.astype(np.complex128))
+    gref, _ = oracle_tor(G)
     n = len(modes)
     for prec in PRECS:
         _, _, tor, a = gbs.subset_sum(ctx, G, "real", prec)

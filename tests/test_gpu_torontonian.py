@@ -13,6 +13,7 @@ import pytest
 import gbs_inputs as gi
 import oracle
 import paper_1810_00900_gb300 as gbs
+from helpers import ref_method
 
 pytestmark = pytest.mark.gpu
 REL = 1e-9
@@ -47,7 +48,7 @@ def test_large_state_patterns_auto_precision(ctx, N):
     st_p, modes24 = gi.single_large_torontonian_workload()
     st = gbs.build_state(ctx, st_p.U, st_p.r, st_p.eta)
     modes = modes24[:N]
-    p_ref, tor_ref, kappa = oracle.click_probability(st_p.U, st_p.r, st_p.eta, modes)
+    p_ref, tor_ref, kappa = oracle.click_probability(st_p.U, st_p.r, st_p.eta, modes, method=ref_method(len(modes)))
     pr = gbs.torontonian(ctx, st, modes, "auto", "real")
     assert abs(pr.p - p_ref) <= REL * abs(p_ref), (N, pr, p_ref)
     assert pr.err_bound <= REL * abs(pr.p)
@@ -61,7 +62,7 @@ def test_lossy_requests_complex_basis(ctx, prec):
         U = gi.haar_unitary(req.M, req.seed)
         r = np.full(req.M, req.r)
         st = gbs.build_state(ctx, U, r, req.eta)
-        p_ref, _, kappa = oracle.click_probability(U, r, req.eta, req.modes)
+        p_ref, _, kappa = oracle.click_probability(U, r, req.eta, req.modes, method=ref_method(req.N))
         pr = gbs.torontonian(ctx, st, req.modes, prec, "complex")
         tol = max(REL, 8 * req.N * {"fp64": 2.0 ** -53, "dd": 2.0 ** -102, "td": 2.0 ** -152}[prec] * kappa)
         assert abs(pr.p - p_ref) <= tol * abs(p_ref) + 1e-300, (i, prec, pr.p, p_ref, kappa)

@@ -16,7 +16,7 @@ import pytest
 import gbs_inputs as gi
 import oracle
 import paper_1810_00900_gb300 as gbs
-from helpers import frac3, real_basis_block
+from helpers import frac3, oracle_tor, real_basis_block
 
 pytestmark = pytest.mark.gpu
 
@@ -42,10 +42,8 @@ def haar_H(N, seed=1, M=200, r=0.8, eta=1.0):
 
 def check(ctx, H, prec, basis):
     n = H.shape[0] // 2
-    ref, ref_abs = oracle.torontonian(H)
     G = real_basis_block(H) if basis == "real" else H
-    if basis == "real":
-        ref, ref_abs = oracle.torontonian(G.astype(np.complex128))
+    ref, ref_abs = oracle_tor(G)
     inc, exc, tor, a = gbs.subset_sum(ctx, G, basis, prec)
     err = abs(frac3(tor) - ref.to_fraction())
     bound = 8 * n * U_OF[prec] * ref_abs
@@ -72,7 +70,7 @@ def test_parity_n14_lossy(ctx, prec, basis):
 @pytest.mark.parametrize("prec", ["dd", "td"])
 def test_parity_n16_relative(ctx, prec):
     G = real_basis_block(haar_H(16))
-    ref, ref_abs = oracle.torontonian(G.astype(np.complex128))  # the same FP64 matrix on both sides
+    ref, ref_abs = oracle_tor(G)  # the same FP64 matrix on both sides
     _, _, tor, _ = gbs.subset_sum(ctx, G, "real", prec)
     rel = abs(float((frac3(tor) - ref.to_fraction()) / ref.to_fraction()))
     # kappa ~ 3e18 here: double-double still has ~1e-13 margin, triple-double far more
@@ -100,7 +98,7 @@ def test_vacuum_gives_zero(ctx):
 
 def test_fp32_diagnostic_runs(ctx):
     H = haar_H(6)
-    ref, ref_abs = oracle.torontonian(H)
+    ref, ref_abs = oracle_tor(H)
     _, _, tor, _ = gbs.subset_sum(ctx, real_basis_block(H), "real", "fp32")
     assert abs(tor[0] + tor[1] - float(ref.to_fraction())) <= 8 * 6 * 2.0 ** -24 * ref_abs
 
@@ -126,7 +124,7 @@ def test_parity_fixed_point(ctx, prec, N):
 def test_parity_fixed_point_n14_lossy_and_n16_relative(ctx, prec):
     check(ctx, haar_H(14, seed=5, M=100, r=0.6, eta=0.5), prec, "real")
     G = real_basis_block(haar_H(16))
-    ref, _ = oracle.torontonian(G.astype(np.complex128))
+    ref, _ = oracle_tor(G)
     _, _, tor, _ = gbs.subset_sum(ctx, G, "real", prec)
     rel = abs(float((frac3(tor) - ref.to_fraction()) / ref.to_fraction()))
     # kappa ~ 3e18: 128 fraction bits leave ~1e-13, 160 and 192 far below 1e-20

@@ -182,8 +182,10 @@ def test_hafnian_known_values():
 
 # ---------------------------------------------- O2 against O1 (the definition) --
 
-@pytest.mark.parametrize("N", [1, 2, 5, 9, 12])
+@pytest.mark.parametrize("N", [1, 2, 5, 9, 12, 14, pytest.param(16, marks=pytest.mark.slow)])
 def test_tree_equals_bruteforce(N):
+    # O2 (the decision tree) against O1 (every subset by its own LU) up to 16 modes:
+    # every GPU comparison beyond 14 modes uses O2.
     st = gi.uniform_squeezed_state(200, 0.8, seed=1)
     Sig = oracle.sigma(oracle.covariance(st.U, st.r, st.eta))
     modes = gi.random_modes(200, 24, seed=1)[:N]
