@@ -42,21 +42,38 @@ def sym(d):
     return d * (d + 1) // 2
 
 
-def tree_flops(q: int, complex_basis: bool) -> int:
-    """FP64 flops of the depth-first tree below one node with q undecided modes,
-    counted from the kernel's formulation: an FMA counts 2, a multiply, add or
-    inverse square root 1.  Per included pivot: det P, rsqrt, the scaled inverse,
-    L = u P^-1 for each of the 2q-2 rows below, and the rank-2 update of the
-    lower triangle of the (2q-2)^2 Schur complement.  A last-level node adds
-    its two leaf terms to the sums (s*g by one FMA, s by one add)."""
-    if q == 1:
-        return 9 if complex_basis else 7
-    d = 2 * q - 2
-    if complex_basis:
-        node = 12 + 20 * d + 16 * (sym(d) - d) + 8 * d
-    else:
-        node = 10 + 6 * d + 4 * sym(d)
-    return node + 2 * tree_flops(q - 1, complex_basis)
+def survey_flops(q: int, complex_basis: bool = False) -> float:
+    """Algorithmic flops of the subtree below a node with q undecided modes, the
+    leading-order count of the method: the include child of a node with t + 1
+    undecided modes does a rank-2 update of 2t rows, 4 t^2 real multiply-adds
+    (8 t^2 flops) in the real basis (complex: 4 t^2 complex multiply-adds, 32 t^2
+    flops), plus one inverse square root and one addition per subset term."""
+    per = 32.0 if complex_basis else 8.0
+    return per * sum(2.0 ** (q - k) * (k - 1) ** 2 for k in range(1, q + 1)) + 2.0 * 2.0 ** q
+
+
+def executed_flops(q: int, Q: int, complex_basis: bool = False) -> float:
+    """FP64 flops the kernels execute below a node with q undecided modes when the
+    last Q levels run in registers (FMA = 2, any other operation = 1; the inverse
+    square root as its three FMAs).  Levels above the register subtree (shared
+    memory) factor the pivot by its adjugate: det, rsqrt, 1/det, the scaled
+    inverse, L = u P^-1 (3 flops per entry of 2t rows) and the update (two FMAs per
+    lower-triangle entry).  The real-basis register levels factor it by Cholesky
+    (two rsqrts, rows w = u R^-T at 4 flops per row); one-mode nodes form det and
+    its rsqrt and add their two leaf terms (one FMA, one add).  Complex entries
+    count 4x the real flops of the same formulas."""
+    def node(k, reg):
+        t = k - 1
+        if k == 1:
+            return 12.0
+        sym2t = t * (2 * t + 1)
+        if reg and not complex_basis:
+            return 18.0 + 8.0 * t + 4.0 * sym2t
+        return 14.0 + 12.0 * t + 4.0 * sym2t
+    total = 0.0
+    for k in range(1, q + 1):
+        total += 2.0 ** (q - k) * node(k, k <= Q)
+    return total * (4.0 if complex_basis else 1.0)
 
 
 class ClockSampler:
@@ -164,13 +181,15 @@ def other_accountings(n: int, step_s: float):
 
 
 def captured_traffic(args, tuning):
-    """DRAM bytes (read + write) per launch of the dominant kernel from the ncu capture summarised in
-    profiles/batch_subtree_kernel_fp64_real_n24.md, when this run launches that same kernel shape
-    (FP64 real basis, N = 24, 6 shared-memory levels, full register depth; the same bytes were
-    counted with one CTA per node and with the persistent grid); None otherwise."""
-    same = (args.prec == "fp64" and args.basis == "real" and args.N == 24 and tuning["sub_e"] == 6
-            and tuning["q_drop"] == 0 and tuning["grid_per_sm"] in (0, 8))
-    return 16741888 + 0 if same else None
+    """DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of the same
+    kernel code and launch shape (FP64 real basis, N = 24, the shared-memory levels and register
+    depth given here); None for any other shape, or once the kernel changed since the capture."""
+    return CAPTURED_TRAFFIC.get((args.prec, args.basis, args.N, tuning["sub_e"], tuning["q_drop"]))
+
+
+# (prec, basis, N, sub_e, q_drop) -> bytes per launch of the subtree kernel, dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of the current kernel code
+CAPTURED_TRAFFIC = {}
 
 
 def whole_job_rate(ws: int, units_per_rank: float, seconds_max: float) -> float:
@@ -178,19 +197,55 @@ def whole_job_rate(ws: int, units_per_rank: float, seconds_max: float) -> float:
     return ws * units_per_rank / seconds_max
 
 
-def cpu_oracle_rate(n_sample: int):
+def cpu_oracle_rate(n_sample: int, threads: int = 0):
     """Oracle subset-terms/s on this host: the decision-tree oracle (~212-bit) on
-    the first n_sample modes of the N = 24 pattern."""
+    the first n_sample modes of the N = 24 pattern (threads <= 0: every core)."""
     import gbs_inputs as gi
     import oracle
     st, modes = gi.single_large_torontonian_workload()
     Sig = oracle.sigma(oracle.covariance(st.U, st.r, st.eta))
     H = oracle.sigma_inv_block(Sig, modes[:n_sample])
-    threads = os.cpu_count() or 1
+    threads = threads if threads > 0 else (os.cpu_count() or 1)
     t0 = time.perf_counter()
     oracle.torontonian(H, "tree", nthreads=threads)
     dt = time.perf_counter() - t0
     return (2 ** n_sample) / dt, dt, threads
+
+
+def cpu_fp64_block(ctx, gbs, st, modes, gpu_terms_per_s):
+    """The same Torontonian in plain FP64 on the host cores: the decision tree in C++ with OpenMP
+    over subtrees (cpu_baseline/), on the very click block the GPU tree starts from (read back
+    from the library), single-core and on every core; median of three runs each."""
+    import cpu_baseline
+    cpu_baseline.build()
+    G = gbs.sigma_inv_block(ctx, st, modes, "real")
+    n = len(modes)
+    cores = cpu_baseline.max_threads()
+    out = {}
+    for name, th in (("single_core", 1), ("all_cores", cores)):
+        runs = [cpu_baseline.torontonian_fp64(G, th, 10) for _ in range(3)]
+        sec = float(np.median([r[2] for r in runs]))
+        out[name] = {"value": 2.0 ** n / sec, "seconds": sec, "threads": th, "tor": runs[-1][0]}
+    return {"metric": "Tor subset-terms/s (FP64, N=%d), host cores" % n, "unit": UNIT, "cores": cores,
+            "kind": "plain FP64 decision tree (same algorithm and precision), OpenMP over 2^10 subtrees",
+            "single_core": out["single_core"], "all_cores": out["all_cores"],
+            "gpu_over_all_cores": gpu_terms_per_s / out["all_cores"]["value"],
+            "gpu_over_single_core": gpu_terms_per_s / out["single_core"]["value"]}
+
+
+def _haar_job(job):
+    import gbs_inputs as gi
+    return gi.haar_unitary(*job)
+
+
+def haar_unitaries(jobs):
+    """Haar unitaries for (M, seed) jobs, built by a pool of fresh (spawned) host processes."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_haar_job, jobs, chunksize=8)
 
 
 def sampler_block(ctx, gbs, gi, n_traj, ws, local, autotune=True):
@@ -296,10 +351,10 @@ def complex_basis_block(ctx, gbs, st, modes, steps, stream, peak):
     t = ctx.tuning("fp64", "complex")
     Q = max(1, min(4 - t["q_drop"], 24))
     q_root = min(24, Q + t["sub_e"])
-    leaf_flops = (2 ** (24 - q_root)) * tree_flops(q_root, True)
+    leaf_flops = (2 ** (24 - q_root)) * survey_flops(q_root, True)
     achieved = leaf_flops / (leaf_ms / max(leaf_n, 1) * 1e-3) / 1e12
     return {"metric": "Tor subset-terms/s (FP64, N=24, complex basis)", "value": 2.0 ** 24 / (ms * 1e-3),
-            "ms_per_evaluation": ms, "tuning": t, "flops_per_term": tree_flops(24, True) / 2.0 ** 24,
+            "ms_per_evaluation": ms, "tuning": t, "survey_flops_per_term": survey_flops(24, True) / 2.0 ** 24,
             "dominant_kernel_tflops": achieved, "frac_of_fp64_peak": achieved / peak}
 
 
@@ -351,7 +406,9 @@ def batched_block(ctx, gbs, gi, n_req, n_err):
     values."""
     reqs = gi.batched_requests(4096)[:n_req]
     t0 = time.perf_counter()
-    states = [gbs.build_state(ctx, gi.haar_unitary(q.M, q.seed), np.full(q.M, q.r), q.eta) for q in reqs]
+    Us = haar_unitaries([(q.M, q.seed) for q in reqs])
+    states = [gbs.build_state(ctx, U, np.full(q.M, q.r), q.eta) for U, q in zip(Us, reqs)]
+    del Us
     t_inputs = time.perf_counter() - t0
     pats = [q.modes for q in reqs]
     terms = float(sum(2 ** q.N for q in reqs))
@@ -398,66 +455,92 @@ def batched_block(ctx, gbs, gi, n_req, n_err):
             "certified": {"seconds": t_cert, "requests_per_s": n_req / t_cert, "precisions": prec_counts,
                           "max_rel_err_bound": worst_bound},
             "input_seconds": t_inputs, "fp32_error_study": err,
-            "workload": "the first %d of 4096 requests: N~U{8..22}, M~U{100,200,400}, r~U[0.4,1.0], "
-                        "eta~U[0.25,1.0], Haar seeded per request" % n_req}
+            "workload": "%d of the 4096 requests: N~U{8..22}, M~U{100,200,400}, r~U[0.4,1.0], "
+                        "eta~U[0.25,1.0], Haar seeded per request; inputs built outside the timed "
+                        "region" % n_req}
 
 
-def served_block(ctx, gbs, gi, n_req, max_attempts, width):
-    """The served dense-subgraph stream: Poisson arrivals (200/s) of postselected sampling jobs on
-    graph-encoded states; latency percentiles of the request loop beside the same requests served
-    one at a time by direct calls (whose results must be identical)."""
-    arrivals, reqs, graphs = gi.served_stream_workload(n_req)
-    cache = {}
-    sts = []
+def _pct(x, q):
+    return float(np.percentile(x, q)) if len(x) else None
+
+
+def served_block(ctx, gbs, gi, plan, max_attempts, width, n_one):
+    """The served dense-subgraph stream: Poisson arrivals of postselected sampling jobs on
+    graph-encoded states (graph, loss, N per request), at several arrival rates -- below the loop's
+    capacity (steady-state latency) and at the stated 200 per second (a burst the loop drains at its
+    capacity).  Latency percentiles are over accepted samples; requests that exhaust their
+    postselection attempts (GBS_EREJECT) are counted and timed apart.  Beside it, the first n_one
+    requests served one at a time through the same loop (one active request, the same attempt
+    width): their measured service times replayed as a single FIFO queue at each rate give the
+    latency without batching across requests; their results must equal the loop's."""
+    n_max = max(n for _, n in plan)
+    _, reqs, graphs = gi.served_stream_workload(n_max)
+    cache, sts = {}, []
     for g, eta, N in reqs:
         if (g, eta, N) not in cache:
             sp = gi.graph_state(graphs[g], 2.0 * N, eta)
             cache[(g, eta, N)] = gbs.build_state(ctx, sp.U, sp.r, sp.eta)
         sts.append(cache[(g, eta, N)])
-    srv = gbs.Server(ctx, arena_bytes=8 << 30, max_active=64, attempt_width=width)
-    t0 = time.perf_counter()
-    tickets = []
-    for i, (a, (g, eta, N)) in enumerate(zip(arrivals, reqs)):
-        dt = t0 + a - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        tickets.append(srv.submit_sample(sts[i], seed=1000 + i, sample_index=0, N_post=N, max_attempts=max_attempts))
-    res = [srv.poll(t, timeout_s=1800) for t in tickets]
-    wall = time.perf_counter() - t0
-    stats = srv.stats()
-    srv.stop()
-    lat = np.array([r["latency_s"] for r in res])
-    ok = sum(1 for r in res if r["status"] == 0)
-    # the same requests, one at a time, in arrival order (single queue)
-    svc = []
-    same = True
-    for i, (g, eta, N) in enumerate(reqs):
+    rows, first_results = [], None
+    for rate, n_req in plan:
+        arrivals, _, _ = gi.served_stream_workload(n_req, rate_hz=rate)
+        srv = gbs.Server(ctx, arena_bytes=8 << 30, max_active=64, attempt_width=width)
+        ctx.host_gaps()
+        t0 = time.perf_counter()
+        tickets = []
+        for i, a in enumerate(arrivals):
+            dt = t0 + a - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit_sample(sts[i], seed=1000 + i, sample_index=0, N_post=reqs[i][2],
+                                             max_attempts=max_attempts))
+        res = [srv.poll(t, timeout_s=1800) for t in tickets]
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+        gap_s, waits = ctx.host_gaps()
+        srv.stop()
+        acc = np.array([r["latency_s"] for r in res if r["status"] == 0])
+        rej = np.array([r["latency_s"] for r in res if r["status"] != 0])
+        rows.append({"rate_hz": rate, "requests": n_req, "accepted": int(acc.size), "rejected": int(rej.size),
+                     "samples_per_s": acc.size / wall, "wall_seconds": wall,
+                     "p50_s": _pct(acc, 50), "p99_s": _pct(acc, 99), "mean_s": float(acc.mean()) if acc.size else None,
+                     "rejected_p50_s": _pct(rej, 50), "rejected_p99_s": _pct(rej, 99),
+                     "loop_busy_fraction": stats["busy_s"] / max(stats["wall_s"], 1e-9),
+                     "host_gap_seconds": gap_s, "host_waits": waits,
+                     "host_gap_fraction_of_busy": gap_s / max(stats["busy_s"], 1e-9)})
+        if first_results is None or len(res) > len(first_results):
+            first_results = res
+    # one at a time: the first n_one requests, each alone in the loop (same attempt width)
+    n_one = min(n_one, len(first_results))
+    srv = gbs.Server(ctx, arena_bytes=8 << 30, max_active=1, attempt_width=width)
+    svc, same = [], True
+    for i in range(n_one):
         t1 = time.perf_counter()
-        pats, _, _, status = gbs.sample(ctx, sts[i], 1, seed=1000 + i, N_post=N, max_attempts=max_attempts,
-                                        check=False)
+        r = srv.poll(srv.submit_sample(sts[i], seed=1000 + i, sample_index=0, N_post=reqs[i][2],
+                                       max_attempts=max_attempts), timeout_s=1800)
         svc.append(time.perf_counter() - t1)
-        if status == 0:
-            same &= res[i]["status"] == 0 and res[i]["clicks"] == np.nonzero(pats[0])[0].tolist()
-        else:
-            same &= res[i]["status"] != 0
-    free_at, lat1 = 0.0, []
-    for a, sv in zip(arrivals, svc):
-        start = max(a, free_at)
-        free_at = start + sv
-        lat1.append(free_at - a)
-    lat1 = np.array(lat1)
+        same &= r["status"] == first_results[i]["status"] and r.get("clicks") == first_results[i].get("clicks")
+    srv.stop()
+    one = []
+    for rate, _ in plan:
+        arrivals, _, _ = gi.served_stream_workload(n_one, rate_hz=rate)
+        free_at, lat_acc = 0.0, []
+        for i, (a, sv) in enumerate(zip(arrivals, svc)):
+            free_at = max(a, free_at) + sv
+            if first_results[i]["status"] == 0:
+                lat_acc.append(free_at - a)
+        one.append({"rate_hz": rate, "requests": n_one, "accepted": len(lat_acc), "p50_s": _pct(lat_acc, 50),
+                    "p99_s": _pct(lat_acc, 99), "samples_per_s": len(lat_acc) / max(free_at, 1e-9)})
     for st in cache.values():
         st.free()
-    return {"metric": "served p50/p99", "requests": n_req, "accepted_samples": ok,
-            "samples_per_s": ok / wall, "wall_seconds": wall,
-            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "loop_busy_fraction": stats["busy_s"] / max(stats["wall_s"], 1e-9),
-            "one_at_a_time": {"samples_per_s": ok / max(free_at, 1e-9), "p50_s": float(np.percentile(lat1, 50)),
-                              "p99_s": float(np.percentile(lat1, 99)), "busy_seconds": float(sum(svc))},
-            "results_identical_to_one_at_a_time": bool(same), "attempt_width": width,
-            "workload": "Poisson arrivals at 200/s; ER graphs n in [100,200] p=0.1 with a planted 20-vertex "
-                        "p=0.9 part; c for mean photon number 2N; eta in {1,0.5,0.25}; one sample postselected "
-                        "on N in [8,20] per request, up to %d attempts" % max_attempts}
+    return {"metric": "served p50/p99", "rates": rows, "attempt_width": width, "max_attempts": max_attempts,
+            "one_at_a_time": one, "one_at_a_time_service_seconds": float(sum(svc)),
+            "one_at_a_time_summary": {"requests": n_one, "samples_per_s": one[-1]["samples_per_s"] if one else None,
+                                      "service_p50_s": _pct(svc, 50), "service_p99_s": _pct(svc, 99)},
+            "results_identical_to_one_at_a_time": bool(same),
+            "workload": "Poisson arrivals; ER graphs n in [100,200] p=0.1 with a planted 20-vertex p=0.9 part; "
+                        "c for mean photon number 2N; eta in {1,0.5,0.25}; one sample postselected on N in "
+                        "[8,20] per request, up to %d attempts, %d at once" % (max_attempts, width)}
 
 
 def subgraph_density(A, nodes):
@@ -501,6 +584,35 @@ def dense_subgraph_block(ctx, gbs, gi, n_samples):
                         "uniform N-subsets" % n_samples}
 
 
+def summary_of(line):
+    """The headline figures of every block in one short object, printed last on the line."""
+    def get(*path):
+        x = line
+        for k in path:
+            if not isinstance(x, dict) or k not in x:
+                return None
+            x = x[k]
+        return x
+    sm = {"fp64_terms_per_s": line.get("value"), "roofline_frac": get("roofline", "frac"),
+          "roofline_frac_executed": get("roofline", "executed", "frac"),
+          "certified_ms": get("certified", "ms_per_evaluation"),
+          "certified_rel_err_bound": get("certified", "rel_err_bound"),
+          "sampler_samples_per_s": get("sampler", "value"),
+          "batched_fp64_requests_per_s": get("batched", "batch_requests_per_s"),
+          "batched_certified_requests_per_s": get("batched", "certified", "requests_per_s"),
+          "batched_requests": get("batched", "requests"),
+          "cpu_fp64_all_cores_terms_per_s": get("cpu_fp64", "all_cores", "value"),
+          "cpu_fp64_single_core_terms_per_s": get("cpu_fp64", "single_core", "value")}
+    served = line.get("served")
+    if isinstance(served, dict):
+        for row in served.get("rates", []):
+            key = "served_%g_per_s" % row["rate_hz"]
+            sm[key] = {k: row.get(k) for k in ("requests", "accepted", "rejected", "p50_s", "p99_s",
+                                               "samples_per_s")}
+        sm["served_one_at_a_time"] = served.get("one_at_a_time_summary")
+    return sm
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -540,13 +652,19 @@ def main():
     ap.add_argument("--N", type=int, default=24)
     ap.add_argument("--cpu-sample", type=int, default=19, help="click count of the oracle's CPU sample")
     ap.add_argument("--ref-sample", type=int, default=16, help="click count per step of --impl reference")
+    ap.add_argument("--cpu-sample-single", type=int, default=14, help="click count of the oracle's one-core sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the certified, paired-FP64 and complex-basis evaluations of the headline tree")
     ap.add_argument("--tuning", default="",
                     help="sub_e,d_top,grid_per_sm,level_threads[,q_drop[,mid_e]] (skips the autotuner)")
     ap.add_argument("--sampler-traj", type=int, default=64, help="forced trajectories of the M=800 sampler run (0: skip)")
-    ap.add_argument("--batched-req", type=int, default=1024, help="requests of the uneven batch (of 4096; 0: skip)")
-    ap.add_argument("--served-req", type=int, default=48, help="requests of the served stream (0: skip)")
+    ap.add_argument("--batched-req", type=int, default=4096, help="requests of the uneven batch (of 4096; 0: skip)")
+    ap.add_argument("--served", default="4:150,8:250,200:500",
+                    help="rate_hz:requests pairs of the served stream runs (empty: skip)")
+    ap.add_argument("--served-one", type=int, default=100,
+                    help="requests served one at a time for the comparison")
     ap.add_argument("--served-attempts", type=int, default=24, help="postselection attempts per served request")
     ap.add_argument("--served-width", type=int, default=8,
                     help="postselection attempts a served request runs at once (1: one after another)")
@@ -595,8 +713,9 @@ def main():
     Q = max(1, min(Q - tuning["q_drop"], args.N))
     q_root = min(args.N, Q + tuning["sub_e"])
     depth = args.N - q_root
-    leaf_flops = (2 ** depth) * tree_flops(q_root, complex_basis)
-    total_flops = tree_flops(args.N, complex_basis)
+    leaf_flops = (2 ** depth) * survey_flops(q_root, complex_basis)
+    leaf_exec = (2 ** depth) * executed_flops(q_root, Q, complex_basis)
+    total_flops = survey_flops(args.N, complex_basis)
     kernel_name = ("batch_subtree_kernel (%d levels expanded in shared memory, then register depth-first %d levels)"
                    % (q_root - Q, Q)) if tuning["sub_e"] else "batch_leaf_kernel (register depth-first, %d levels)" % Q
 
@@ -636,6 +755,7 @@ def main():
     value = whole_job_rate(ws, args.steps * terms, dev_ms * 1e-3)
     leaf_avg_s = leaf_ms / max(leaf_n, 1) * 1e-3
     achieved = leaf_flops / leaf_avg_s / 1e12
+    achieved_exec = leaf_exec / leaf_avg_s / 1e12
     peak = peak_gflops / 1e3
 
     # e2e: the same step through the public API from pinned host buffers, state build included.
@@ -672,13 +792,18 @@ def main():
             "l2": "flushed between steps (256 MB write); tree level buffers also exceed L2",
             "parallelism": "replicas" if ws > 1 else "single GPU",
             "tuning": tuning, "autotune_candidates": len(tune_report),
+            "autotune_fastest": sorted(tune_report, key=lambda c: c["ms"])[:5] if tune_report else [],
         },
         "roofline": {
             "bound": "alu", "kernel": kernel_name,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "peak_source": "FP64 DFMA-chain kernel measured in this run (gbs_measure_fp64_peak)",
             "traffic": captured_traffic(args, tuning), "traffic_unit": "bytes per launch",
+            "traffic_source": "stored ncu capture of this kernel code and launch shape (not measured in this run)",
+            "flop_model": "8 t^2 flops per rank-2 update of 2t rows (real basis) + rsqrt and add per subset term",
             "flops_per_launch": leaf_flops, "leaf_ms_avg": leaf_avg_s * 1e3,
+            "executed": {"flops_per_launch": leaf_exec, "achieved": achieved_exec, "frac": achieved_exec / peak,
+                         "model": "every FP64 operation the kernel executes (FMA = 2, other = 1, rsqrt = 3 FMAs)"},
             "step_flops": total_flops,
             "step_tflops": total_flops * args.steps / (dev_ms * 1e-3) / 1e12,
             "other_accountings": other_accountings(args.N, dev_ms * 1e-3 / args.steps),
@@ -688,7 +813,7 @@ def main():
         "clocks": clk,
         "result": {"p": results[-1].p, "kappa": results[-1].kappa, "prec": results[-1].prec},
     }
-    if args.prec == "fp64" and args.N == 24:
+    if args.prec == "fp64" and args.N == 24 and not args.no_extras:
         line["certified"] = certified_block(ctx, gbs, st, modes, max(3, args.steps // 2), stream)
         line["paired_fp64"] = paired_block(ctx, gbs, st, modes, max(3, args.steps // 2), stream, line["certified"],
                                            results[-1])
@@ -697,8 +822,9 @@ def main():
         line["sampler"] = sampler_block(ctx, gbs, gi, args.sampler_traj, ws, local, autotune=not args.no_autotune)
     if args.batched_req > 0:
         line["batched"] = batched_block(ctx, gbs, gi, args.batched_req, 48)
-    if args.served_req > 0:
-        line["served"] = served_block(ctx, gbs, gi, args.served_req, args.served_attempts, args.served_width)
+    if args.served:
+        plan = [(float(x.split(":")[0]), int(x.split(":")[1])) for x in args.served.split(",")]
+        line["served"] = served_block(ctx, gbs, gi, plan, args.served_attempts, args.served_width, args.served_one)
     if args.walltime_m:
         line["walltime"] = walltime_block(ctx, gbs, gi, [int(x) for x in args.walltime_m.split(",")])
     if args.dense_samples > 0:
@@ -707,9 +833,15 @@ def main():
         import oracle
         oracle.build()
         rate, dt, threads = cpu_oracle_rate(args.cpu_sample)
+        rate1, dt1, _ = cpu_oracle_rate(args.cpu_sample_single, threads=1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": "N=%d sub-pattern of the same state (2^%d terms, %.1f s, ~212-bit "
-                                          "decision-tree oracle)" % (args.cpu_sample, args.cpu_sample, dt)}
+                                          "decision-tree oracle)" % (args.cpu_sample, args.cpu_sample, dt),
+                                "single_core": {"value": rate1, "sample": "N=%d sub-pattern, %.1f s, one thread"
+                                                % (args.cpu_sample_single, dt1)}}
+        if args.prec == "fp64" and args.basis == "real":
+            line["cpu_fp64"] = cpu_fp64_block(ctx, gbs, st, modes, value)
+    line["summary"] = summary_of(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     st.free()

@@ -126,6 +126,13 @@ long long gbs_ctx_launch_count(const gbs_ctx* ctx);
  * device time (ms) and the number of timed launches, and resets them. */
 gbs_status gbs_ctx_enable_timing(gbs_ctx* ctx, int enable);
 gbs_status gbs_ctx_kernel_time(gbs_ctx* ctx, double* total_ms, long long* launches);
+/* Host gaps of the context: the summed wall time (s) from the return of each
+ * host wait on the context stream (a synchronisation to read results back)
+ * to the next kernel launch, while the stream sits empty, and the number of
+ * such waits; both reset on read.  A lower bound on the device idle time the
+ * host side causes (launches slower than the kernels they follow add more).
+ * The paper has no counterpart. */
+gbs_status gbs_ctx_host_gaps(gbs_ctx* ctx, double* seconds, long long* waits);
 
 /* FP64 throughput of this GPU, measured now: a full grid of independent
  * dependent-FMA chains (no memory traffic), best of three timed launches on the
@@ -297,10 +304,12 @@ gbs_status gbs_server_stop(gbs_ctx* ctx);
 /* Queue a request; *ticket identifies it.  Errors: GBS_EINVAL (loop not running,
  * bad descriptor), GBS_ENOMEM (footprint larger than the whole arena). */
 gbs_status gbs_submit(gbs_ctx* ctx, const gbs_request* req, uint64_t* ticket);
-/* Wait up to timeout_us microseconds (0: do not wait, < 0: until done) for a
- * ticket.  GBS_OK: *out holds the result (its own status in out->status) and
- * the ticket is consumed; GBS_PENDING: not finished; GBS_ENOTFOUND: unknown or
- * already consumed ticket. */
+/* Wait up to timeout_us microseconds for a ticket (0: do not wait; < 0: until
+ * done, but at most 10 minutes).  GBS_OK: *out holds the result (its own status
+ * in out->status) and the ticket is consumed; GBS_PENDING: not finished within
+ * a bound the caller gave; GBS_ETIMEDOUT: not finished within the 10 minutes of
+ * a negative bound (the ticket stays valid); GBS_ENOTFOUND: unknown or already
+ * consumed ticket. */
 gbs_status gbs_poll(gbs_ctx* ctx, uint64_t ticket, gbs_result* out, int64_t timeout_us);
 gbs_status gbs_server_stats_get(gbs_ctx* ctx, gbs_server_stats* out);
 

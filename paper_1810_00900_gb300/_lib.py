@@ -98,6 +98,7 @@ def load() -> ctypes.CDLL:
         "gbs_ctx_launch_count": (ctypes.c_longlong, [_vp]),
         "gbs_ctx_enable_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
         "gbs_ctx_kernel_time": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+        "gbs_ctx_host_gaps": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
         "gbs_measure_fp64_peak": (ctypes.c_int, [_vp, _dp]),
         "gbs_build_state": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, ctypes.POINTER(_vp)]),
         "gbs_state_from_V": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(_vp)]),
@@ -223,6 +224,13 @@ class Context:
         n = ctypes.c_longlong()
         self.check(self.L.gbs_ctx_kernel_time(self.h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def host_gaps(self):
+        """(seconds, waits) of host gaps since the last call (gbs_ctx_host_gaps)."""
+        s = ctypes.c_double()
+        n = ctypes.c_longlong()
+        self.check(self.L.gbs_ctx_host_gaps(self.h, ctypes.byref(s), ctypes.byref(n)))
+        return s.value, n.value
 
 
 class State:

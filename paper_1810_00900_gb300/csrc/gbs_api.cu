@@ -17,6 +17,14 @@ gbs_status set_error(gbs_ctx* ctx, gbs_status st, const std::string& msg) {
   return st;
 }
 
+gbs_status stream_sync(gbs_ctx* ctx) {
+  const gbs_status st = stream_sync(ctx);
+  ctx->gap_since = std::chrono::steady_clock::now();
+  ctx->gap_open = true;
+  ctx->gap_waits++;
+  return st;
+}
+
 gbs_status check_cuda(gbs_ctx* ctx, cudaError_t e, const char* what) {
   if (e == cudaSuccess) return GBS_OK;
   char buf[256];
@@ -270,6 +278,16 @@ gbs_status gbs_ctx_kernel_time(gbs_ctx* ctx, double* total_ms, long long* launch
   return GBS_OK;
 }
 
+gbs_status gbs_ctx_host_gaps(gbs_ctx* ctx, double* seconds, long long* waits) {
+  if (!ctx) return GBS_EINVAL;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (seconds) *seconds = ctx->gap_s;
+  if (waits) *waits = ctx->gap_waits;
+  ctx->gap_s = 0.0;
+  ctx->gap_waits = 0;
+  return GBS_OK;
+}
+
 gbs_status gbs_build_state(gbs_ctx* ctx, int M, const double* U, const double* r, double eta, double* V_out,
                            gbs_state** st) {
   if (!ctx) return GBS_EINVAL;
@@ -318,7 +336,7 @@ gbs_status gbs_sigma_inv_block(gbs_ctx* ctx, const gbs_state* st, const int* mod
   std::vector<double> packed(ne * (real ? 1 : 2));
   if ((e = check_cuda(ctx, cudaMemcpyAsync(packed.data(), ctx->hbuf.ptr, ne * esz, cudaMemcpyDeviceToHost, ctx->stream),
                       "readback")) ||
-      (e = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync")))
+      (e = stream_sync(ctx)))
     return e;
   // unpack the lower triangle into the full Hermitian / symmetric matrix
   for (int a = 0; a < D; ++a)

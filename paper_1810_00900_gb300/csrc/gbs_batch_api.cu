@@ -17,7 +17,7 @@ gbs_status stage_begin(gbs_ctx* ctx, size_t bytes) {
   bytes = (bytes + 4096 + 255) / 256 * 256;
   if (bytes > ctx->stage_cap) {
     gbs_status st;
-    if ((st = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync"))) return st;
+    if ((st = stream_sync(ctx))) return st;
     size_t cap = std::max(bytes, ctx->stage_cap * 2);
     cap = std::max(cap, (size_t)1 << 20);
     if (ctx->stage_host) cudaFreeHost(ctx->stage_host);
@@ -263,7 +263,7 @@ gbs_status batch_eval(gbs_ctx* ctx, int prec, bool real, int ntrees, const Batch
   if ((st = check_cuda(ctx, cudaGetLastError(), "finish"))) return st;
   if ((st = check_cuda(ctx, cudaMemcpyAsync(host_out, po, n * sizeof(ProbOut), cudaMemcpyDeviceToHost, ctx->stream),
                        "readback")) ||
-      (st = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync")))
+      (st = stream_sync(ctx)))
     return st;
   if (ctx->timing && ctx->leaf_timer.pending) {
     float ms = 0.f;
@@ -391,7 +391,7 @@ gbs_status probs_batch(gbs_ctx* ctx, int nreq, const gbs_state* const* states, c
     if ((st = check_cuda(ctx, cudaMemcpyAsync(est.data(), d_est, est.size() * sizeof(double), cudaMemcpyDeviceToHost,
                                               ctx->stream),
                          "kappa estimate")) ||
-        (st = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync")))
+        (st = stream_sync(ctx)))
       return st;
     for (size_t i = 0; i < todo.size(); ++i) lk[todo[i]] = est[i];
   }

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <chrono>
 #include <map>
 #include <mutex>
 #include <string>
@@ -87,6 +88,12 @@ struct gbs_ctx {
   gbs::KernelTimer leaf_timer;
   std::atomic<long long> launches{0};
   int sm_count = 0;
+  // host gaps: time from the return of a host wait on the stream (stream_sync)
+  // to the next kernel launch, while the stream sits empty
+  bool gap_open = false;
+  std::chrono::steady_clock::time_point gap_since;
+  double gap_s = 0.0;
+  long long gap_waits = 0;
 
   // batched-engine launch parameters per (precision, basis): [prec][real]
   gbs::BatchTune tune[gbs::kPrecLast + 1][2];  // [gbs_prec][basis is real]
@@ -121,7 +128,15 @@ gbs_status dev_alloc(gbs_ctx* ctx, DevBuf& b, size_t bytes);
 gbs_status dev_reserve(gbs_ctx* ctx, DevBuf& b, size_t bytes);  // grow-only
 void dev_free(gbs_ctx* ctx, DevBuf& b);
 void cache_release(gbs_ctx* ctx);  // return cached device blocks to CUDA (cudaFree)
-inline void count_launch(gbs_ctx* ctx, long long n = 1) { ctx->launches += n; }
+inline void count_launch(gbs_ctx* ctx, long long n = 1) {
+  ctx->launches += n;
+  if (ctx->gap_open) {
+    ctx->gap_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - ctx->gap_since).count();
+    ctx->gap_open = false;
+  }
+}
+// Wait for the context stream to drain (to read results back) and start a host gap.
+gbs_status stream_sync(gbs_ctx* ctx);
 
 // Staging arena: stage_begin() makes room for `bytes` (synchronising first if it
 // must grow) and resets it; stage() copies host data into the next region and

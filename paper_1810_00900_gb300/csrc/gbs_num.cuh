@@ -207,7 +207,11 @@ GBS_HD float fms(float x, float a, float b) { return fmaf(-a, b, x); }
 GBS_HD float fpa(float x, float a, float b) { return fmaf(a, b, x); }
 GBS_HD double to_double(double a) { return a; }
 GBS_HD double to_double(float a) { return (double)a; }
+#ifdef GBS_EXPERIMENT_CUDA_RSQRT
+__device__ __forceinline__ double rsqrt_(double a) { return rsqrt(a); }
+#else
 __device__ __forceinline__ double rsqrt_(double a) { return rsqrt_f64(a); }
+#endif
 __device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
 
 template <class T> GBS_HD T from_double(double a);

@@ -489,7 +489,7 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
   if ((e = check_cuda(ctx, cudaMemcpyAsync(dec.data(), dout, act.size() * sizeof(DecideOut), cudaMemcpyDeviceToHost,
                                            ctx->stream),
                       "decide readback")) ||
-      (e = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync")))
+      (e = stream_sync(ctx)))
     return e;
   // ---- bookkeeping, postselection, conditioning of the dark modes
   std::vector<CondItem> ci;
@@ -595,7 +595,7 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
     if (!any) break;
     if ((e = sampler_advance(ctx, ptrs, prec, stt))) return fail(e);
   }
-  if ((e = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync"))) return fail(e);
+  if ((e = stream_sync(ctx))) return fail(e);
   dev_free(ctx, work);
   bool all = true;
   for (int t = 0; t < T; ++t) {

@@ -39,6 +39,9 @@ namespace {
 
 using clock_t_ = std::chrono::steady_clock;
 
+// Longest wait of gbs_poll when the caller passes a negative bound (10 minutes).
+constexpr int64_t kPollDefaultUs = 600LL * 1000 * 1000;
+
 // A sampling request runs up to `width` postselection attempts at once, one per
 // trajectory slot.  outcome[a] records attempt a (0 unknown, 1 rejected,
 // 2 accepted with its clicks); the request's result is the lowest accepted
@@ -465,10 +468,10 @@ gbs_status gbs_poll(gbs_ctx* ctx, uint64_t ticket, gbs_result* out, int64_t time
   Req* q = it->second;
   if (!q->done && timeout_us != 0) {
     auto pred = [&] { return q->done || sv->stop; };
-    if (timeout_us < 0)
-      sv->cv_done.wait(lk, pred);
-    else
-      sv->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), pred);
+    // a negative bound still ends: after kPollDefaultUs the call gives up
+    const int64_t us = timeout_us < 0 ? kPollDefaultUs : timeout_us;
+    sv->cv_done.wait_for(lk, std::chrono::microseconds(us), pred);
+    if (!q->done && timeout_us < 0) return GBS_ETIMEDOUT;
   }
   if (!q->done) return GBS_PENDING;
   *out = q->res;

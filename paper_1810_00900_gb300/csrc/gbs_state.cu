@@ -250,7 +250,7 @@ gbs_status ensure_V(gbs_ctx* ctx, gbs_state* st) {
                                                                 (cplx<double>*)st->V.ptr);
   count_launch(ctx, 2);
   if ((e = check_cuda(ctx, cudaGetLastError(), "build V")) ||
-      (e = check_cuda(ctx, cudaStreamSynchronize(s), "sync"))) {
+      (e = stream_sync(ctx))) {
     dev_free(ctx, tmp);
     return e;
   }
@@ -300,12 +300,12 @@ gbs_status state_build(gbs_ctx* ctx, int M, const double* U, const double* r, do
   if ((e = check_cuda(ctx, cudaGetLastError(), "state kernels"))) return fail(e);
   if ((e = check_cuda(ctx, cudaMemcpyAsync(&st->logdet_sigma, ld_out, 8, cudaMemcpyDeviceToHost, s), "copy logdet")))
     return fail(e);
-  if ((e = check_cuda(ctx, cudaStreamSynchronize(s), "sync"))) return fail(e);
+  if ((e = stream_sync(ctx))) return fail(e);
   dev_free(ctx, tmp);
   if (V_out) {
     if ((e = ensure_V(ctx, st))) return fail(e);
     if ((e = check_cuda(ctx, cudaMemcpyAsync(V_out, st->V.ptr, 4 * MM * 16, cudaMemcpyDeviceToHost, s), "copy V")) ||
-        (e = check_cuda(ctx, cudaStreamSynchronize(s), "sync")))
+        (e = stream_sync(ctx)))
       return fail(e);
   }
   *out = st;
@@ -357,7 +357,7 @@ gbs_status state_from_V(gbs_ctx* ctx, int M, const double* V, gbs_state** out) {
   int hstatus = 0;
   if ((e = check_cuda(ctx, cudaMemcpyAsync(&st->logdet_sigma, pv + 2 * D, 8, cudaMemcpyDeviceToHost, s), "copy")) ||
       (e = check_cuda(ctx, cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, s), "copy")) ||
-      (e = check_cuda(ctx, cudaStreamSynchronize(s), "sync")))
+      (e = stream_sync(ctx)))
     return fail(e);
   if (hstatus) return fail(set_error(ctx, GBS_ENOTPD, "gbs_state_from_V: Sigma = V + I/2 is not positive definite"));
   dev_free(ctx, X2);

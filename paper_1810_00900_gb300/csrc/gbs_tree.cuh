@@ -292,6 +292,11 @@ __device__ __forceinline__ void pair_single(const double (&c)[sym(D)], double s,
 }
 
 // ----------------------------------------------- register depth-first ----
+#ifdef GBS_EXPERIMENT_ADJUGATE
+constexpr bool kExperimentAdjugate = true;
+#else
+constexpr bool kExperimentAdjugate = false;
+#endif
 // Node with Q undecided modes whose matrix is the view c[tri(OFF + i, OFF + j)]
 // of an array of dimension D; NEG = odd number of exclusions above it.  PAIR:
 // the last two levels as cancellation-free groups (above; E = double only).
@@ -304,7 +309,7 @@ struct Dfs {
     if constexpr (PAIR && Q <= 2) {
       static_assert(std::is_same<E, double>::value, "the paired last levels are FP64 real-basis only");
       if constexpr (Q == 2) pair_group<D, OFF, NEG>(c, s, acc); else pair_single<D, OFF, NEG>(c, s, acc);
-    } else if constexpr (std::is_same<E, double>::value) {
+    } else if constexpr (std::is_same<E, double>::value && !kExperimentAdjugate) {
       // FP64 real basis, the pivot block factored as P = R R^T (Cholesky):
       //   r0 = p00^(-1/2), w = p10 r0, d1 = p11 - w^2, r1 = d1^(-1/2),
       //   det(P)^(-1/2) = r0 r1,
@@ -314,13 +319,13 @@ struct Dfs {
       // costs two fused multiply-adds.  A one-mode node needs only det(P).
       const double p00 = c[tri(OFF, OFF)], p11 = c[tri(OFF + 1, OFF + 1)], p10 = c[tri(OFF + 1, OFF)];
       if constexpr (Q == 1) {
-        const double g = rsqrt_f64(fma(p00, p11, -p10 * p10));
+        const double g = rsqrt_(fma(p00, p11, -p10 * p10));
         if (NEG) { acc.in = fma(s, g, acc.in); acc.ep += s; } else { acc.ip = fma(s, g, acc.ip); acc.en += s; }
       } else {
         constexpr int DN = 2 * Q - 2;
-        const double r0 = rsqrt_f64(p00);
+        const double r0 = rsqrt_(p00);
         const double w = p10 * r0;
-        const double r1 = rsqrt_f64(fma(-w, w, p11));
+        const double r1 = rsqrt_(fma(-w, w, p11));
         const double g = r0 * r1;
         const double kap = -w * g;
         double w0[DN], w1[DN];

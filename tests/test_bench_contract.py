@@ -33,7 +33,7 @@ def test_reference_arm_line():
 @pytest.mark.gpu
 def test_gpu_arm_line():
     d = run_bench("--steps", "3", "--warmup", "3", "--N", "16", "--no-autotune", "--sampler-traj", "0",
-                  "--batched-req", "0", "--served-req", "0", "--walltime-m=", "--dense-samples", "0",
+                  "--batched-req", "0", "--served=", "--walltime-m=", "--dense-samples", "0",
                   "--cpu-sample", "12")
     assert BASE_KEYS <= set(d) and {"roofline", "gpu_launches", "clocks"} <= set(d)
     r = d["roofline"]
