@@ -18,7 +18,7 @@ gbs_status set_error(gbs_ctx* ctx, gbs_status st, const std::string& msg) {
 }
 
 gbs_status stream_sync(gbs_ctx* ctx) {
-  const gbs_status st = stream_sync(ctx);
+  const gbs_status st = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync");
   ctx->gap_since = std::chrono::steady_clock::now();
   ctx->gap_open = true;
   ctx->gap_waits++;
