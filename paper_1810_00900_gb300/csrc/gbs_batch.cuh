@@ -324,21 +324,39 @@ __global__ void __launch_bounds__(128, leaf_min_blocks<E>::value) batch_leaf_ker
   for (long long vb = blockIdx.x; vb < total_blocks; vb += gridDim.x) {
     const LeafSeg sg = segs[find_seg(segs, nseg, vb, &LeafSeg::block_begin)];
     const long long node = (vb - sg.block_begin) * blockDim.x + threadIdx.x;
-    Red inc = red_zero<Red>(), exc = red_zero<Red>();
-    double asum = 0.0;
-    if (node < sg.count) {
-      const E* nodes = (sg.buf ? buf1 : buf0) + sg.base;
-      E c[sym(2 * Q)];
+    if constexpr (std::is_same<Acc, double>::value) {
+      Sums<double> a = sums_zero<double>();
+      if (node < sg.count) {
+        const E* nodes = (sg.buf ? buf1 : buf0) + sg.base;
+        E c[sym(2 * Q)];
 #pragma unroll
-      for (int e = 0; e < sym(2 * Q); ++e) c[e] = ld_node(nodes, e, sg.count, node);
-      const typename scale_of<E>::type s = (sg.buf ? s1 : s0)[sg.s_base + node];
-      if (!subtree_sums<E, Q, PAIR>(c, s, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
-      if ((sg.depth - __popcll((unsigned long long)node)) & 1) {
-        inc = red_neg(inc);
-        exc = red_neg(exc);
+        for (int e = 0; e < sym(2 * Q); ++e) c[e] = ld_node(nodes, e, sg.count, node);
+        const typename scale_of<E>::type s = (sg.buf ? s1 : s0)[sg.s_base + node];
+        const bool ok = subtree_run<E, Q, PAIR>(c, s, a);
+        if (!ok || !isfinite((a.ip + a.in) + (a.ep + a.en))) atomicExch(status + sg.tree, bad_status<T>());
+        if ((sg.depth - __popcll((unsigned long long)node)) & 1) {
+          const double t0 = a.ip, t1 = a.ep;
+          a.ip = a.in; a.in = t0; a.ep = a.en; a.en = t1;
+        }
       }
+      block_reduce_sums<PAIR>(a.ip, a.in, a.ep, a.en, parts + vb);
+    } else {
+      Red inc = red_zero<Red>(), exc = red_zero<Red>();
+      double asum = 0.0;
+      if (node < sg.count) {
+        const E* nodes = (sg.buf ? buf1 : buf0) + sg.base;
+        E c[sym(2 * Q)];
+#pragma unroll
+        for (int e = 0; e < sym(2 * Q); ++e) c[e] = ld_node(nodes, e, sg.count, node);
+        const typename scale_of<E>::type s = (sg.buf ? s1 : s0)[sg.s_base + node];
+        if (!subtree_sums<E, Q, PAIR>(c, s, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<T>());
+        if ((sg.depth - __popcll((unsigned long long)node)) & 1) {
+          inc = red_neg(inc);
+          exc = red_neg(exc);
+        }
+      }
+      block_reduce_store(inc, exc, asum, parts + vb);
     }
-    block_reduce_store(inc, exc, asum, parts + vb);
     __syncthreads();
   }
 }
@@ -390,22 +408,39 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
     bool bad = false;
     smem_expand<E>(src, dst, ssrc, sdst, pm10, pq00, pq11, nodes, q, sg.e_levels, bad);
     if (bad) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
-    Red inc = red_zero<Red>(), exc = red_zero<Red>();
-    double asum = 0.0;
     const int t = threadIdx.x;
-    if (t < nodes) {
-      E c[sym(2 * Q)];
+    if constexpr (std::is_same<Acc, double>::value) {
+      Sums<double> a = sums_zero<double>();
+      if (t < nodes) {
+        E c[sym(2 * Q)];
 #pragma unroll
-      for (int e = 0; e < sym(2 * Q); ++e) c[e] = src[e * nodes + t];
-      const S sv = ssrc[t];
-      if (!subtree_sums<E, Q, PAIR>(c, sv, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
-      const unsigned long long gnode = ((unsigned long long)root << sg.e_levels) | (unsigned long long)t;
-      if ((sg.depth_leaf - __popcll(gnode)) & 1) {
-        inc = red_neg(inc);
-        exc = red_neg(exc);
+        for (int e = 0; e < sym(2 * Q); ++e) c[e] = src[e * nodes + t];
+        const bool ok = subtree_run<E, Q, PAIR>(c, ssrc[t], a);
+        if (!ok || !isfinite((a.ip + a.in) + (a.ep + a.en))) atomicExch(status + sg.tree, bad_status<T>());
+        const unsigned long long gnode = ((unsigned long long)root << sg.e_levels) | (unsigned long long)t;
+        if ((sg.depth_leaf - __popcll(gnode)) & 1) {
+          const double t0 = a.ip, t1 = a.ep;
+          a.ip = a.in; a.in = t0; a.ep = a.en; a.en = t1;
+        }
       }
+      block_reduce_sums<PAIR>(a.ip, a.in, a.ep, a.en, parts + vb);
+    } else {
+      Red inc = red_zero<Red>(), exc = red_zero<Red>();
+      double asum = 0.0;
+      if (t < nodes) {
+        E c[sym(2 * Q)];
+#pragma unroll
+        for (int e = 0; e < sym(2 * Q); ++e) c[e] = src[e * nodes + t];
+        const S sv = ssrc[t];
+        if (!subtree_sums<E, Q, PAIR>(c, sv, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<T>());
+        const unsigned long long gnode = ((unsigned long long)root << sg.e_levels) | (unsigned long long)t;
+        if ((sg.depth_leaf - __popcll(gnode)) & 1) {
+          inc = red_neg(inc);
+          exc = red_neg(exc);
+        }
+      }
+      block_reduce_store(inc, exc, asum, parts + vb);
     }
-    block_reduce_store(inc, exc, asum, parts + vb);
     __syncthreads();
   }
 }

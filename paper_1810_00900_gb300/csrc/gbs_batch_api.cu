@@ -177,7 +177,7 @@ __global__ void kappa_estimate_kernel(const BatchTree* __restrict__ trees, int n
 
 __global__ void batch_finish_kernel(const TreeOut* __restrict__ outs, const int* __restrict__ status,
                                     const double* __restrict__ logdet, const int* __restrict__ nmodes, double u,
-                                    int ntrees, ProbOut* __restrict__ po) {
+                                    double extra, int ntrees, ProbOut* __restrict__ po) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ntrees) return;
   const TreeOut& o = outs[t];
@@ -193,7 +193,7 @@ __global__ void batch_finish_kernel(const TreeOut* __restrict__ outs, const int*
   r.abs_sum = o.abs;
   const double tv = tor.x0 + (tor.x1 + tor.x2);
   r.kappa = tv != 0.0 ? o.abs / fabs(tv) : INFINITY;
-  r.err = 4.0 * (nmodes[t] > 0 ? nmodes[t] : 1) * u * o.abs * sc;
+  r.err = (4.0 * (nmodes[t] > 0 ? nmodes[t] : 1) + extra) * u * o.abs * sc;
   for (int i = 0; i < 3; ++i) { r.inc[i] = o.inc[i]; r.exc[i] = o.exc[i]; }
   r.status = status[t];
   r.pad = 0;
@@ -258,7 +258,8 @@ gbs_status batch_eval(gbs_ctx* ctx, int prec, bool real, int ntrees, const Batch
   if ((st = check_cuda(ctx, cudaMemsetAsync(status, 0, n * sizeof(int), ctx->stream), "memset"))) return st;
   if ((st = batch_variant(ctx, prec, real, ntrees, trees, roots_dev, outs, status))) return st;
   batch_finish_kernel<<<(ntrees + 127) / 128, 128, 0, ctx->stream>>>(
-      outs, status, (const double*)d_logdet, (const int*)d_n, unit_roundoff_b(prec), ntrees, po);
+      outs, status, (const double*)d_logdet, (const int*)d_n, unit_roundoff_b(prec),
+      err_factor(prec, 1) - err_factor(GBS_PREC_TD, 1), ntrees, po);
   count_launch(ctx);
   if ((st = check_cuda(ctx, cudaGetLastError(), "finish"))) return st;
   if ((st = check_cuda(ctx, cudaMemcpyAsync(host_out, po, n * sizeof(ProbOut), cudaMemcpyDeviceToHost, ctx->stream),

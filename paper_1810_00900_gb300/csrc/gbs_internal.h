@@ -208,6 +208,16 @@ double unit_of(int prec);
 bool fx_ok_inverse(const gbs_state* st, int n);
 bool fx_ok_sigma(const gbs_state* st, int n);
 
+// Error model of a subset tree over n modes in precision prec: |dTor| <=
+// err_factor * unit * sum|terms|, with 4 n units per term (n rank-2 Schur steps
+// and one inverse square root) and, for the FP64 family, 24 more for the FP64
+// sums of the non-negative sign-split partials (up to 15 within a thread's
+// register subtree, 5 across a warp, margin for the double-double stages).
+inline double err_factor(int prec, int n) {
+  const double base = 4.0 * (n > 1 ? n : 1);
+  return (prec == GBS_PREC_FP64 || prec == GBS_PREC_FP64P || prec == GBS_PREC_FP32_DIAG) ? base + 24.0 : base;
+}
+
 // Up to 32 click modes passed by value as a kernel argument.
 struct ModeList {
   int m[32];

@@ -337,7 +337,7 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
     const double margin[4] = {4.0, 2.0, 1.0, 1.0};
     for (int l = 0; l < 4; ++l) {
       if (is_fixed_point(ladder[l]) && !fx_ok_sigma(t->st, n)) continue;
-      if (4.0 * std::max(n, 1) * unit_of(ladder[l]) * kp * margin[l] < TOL) return ladder[l];
+      if (err_factor(ladder[l], n) * unit_of(ladder[l]) * kp * margin[l] < TOL) return ladder[l];
     }
     return (int)GBS_PREC_TD;
   };
@@ -420,7 +420,7 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
       if (q.res.status == kStatusRange)
         return set_error(ctx, GBS_EPRECISION, "sampler: a fixed-point tree left its range");
       if (q.res.status) return set_error(ctx, GBS_ENOTPD, "sampler: a pivot block is not positive definite");
-      const double u = unit_of(q.prec), n = std::max(q.n, 1);
+      const double u = unit_of(q.prec), n = err_factor(q.prec, q.n) / 4.0;
       double dp;
       if (q.half) {
         const double tor = fabs(q.res.tor[0]);
@@ -467,7 +467,7 @@ gbs_status sampler_advance(gbs_ctx* ctx, const std::vector<Trajectory*>& jobs, i
     d.half = q.half;
     d.M = t->M;
     di[i] = d;
-    const double u = unit_of(q.prec), n = std::max(q.n, 1);
+    const double u = unit_of(q.prec), n = err_factor(q.prec, q.n) / 4.0;
     if (q.half) {
       const double tor = fabs(q.res.tor[0]);
       t->kappa_prev = q.res.abs_sum / std::max(tor, 1e-300);

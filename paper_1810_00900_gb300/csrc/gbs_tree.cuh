@@ -413,6 +413,51 @@ __device__ __forceinline__ bool subtree_sums(const E (&c)[sym(2 * Q)], const typ
   }
 }
 
+// Register subtree of one node into per-thread sign-split sums (added to acc);
+// false if a pivot was not positive definite.
+template <class E, int Q, bool PAIR = false>
+__device__ __forceinline__ bool subtree_run(const E (&c)[sym(2 * Q)], const typename scale_of<E>::type& s,
+                                            Sums<typename acc_traits<typename real_of<E>::type>::Acc>& a) {
+  bool bad = false;
+  Dfs<E, Q, 2 * Q, 0, false, PAIR>::run(c, s, a, bad);
+  return !bad;
+}
+
+// Block reduction of per-thread FP64 sign-split sums (ip, in, ep, en) into one
+// double-double partial.  In a plain tree the four sums are non-negative, so a
+// warp adds them in FP64 (five rounding levels, relative error <= 5 u each, no
+// cancellation); lane 0 then forms inc = ip - in and exc = ep - en exactly
+// (TwoSum) and one thread adds the warps' partials in double-double.  This
+// keeps the reduction at ~20 FP64 additions per thread instead of the ~110 of
+// a double-double warp reduction.  PAIR (cancellation-free last levels): ip
+// and in carry the signed group values, ep + en the group magnitudes.
+template <bool PAIR>
+__device__ __forceinline__ void block_reduce_sums(double ip, double in, double ep, double en, Partial<dd>* out) {
+  __shared__ dd s_inc[32], s_exc[32];
+  __shared__ double s_abs[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    ip += __shfl_down_sync(0xffffffffu, ip, off);
+    in += __shfl_down_sync(0xffffffffu, in, off);
+    ep += __shfl_down_sync(0xffffffffu, ep, off);
+    en += __shfl_down_sync(0xffffffffu, en, off);
+  }
+  if (lane == 0) {
+    s_inc[warp] = red_diff(ip, in, (dd*)nullptr);
+    s_exc[warp] = PAIR ? dd_make(0.0) : red_diff(ep, en, (dd*)nullptr);
+    s_abs[warp] = PAIR ? ep + en : (ip + in) + (ep + en);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    dd a = s_inc[0], b = s_exc[0];
+    double c = s_abs[0];
+    for (int w = 1; w < nw; ++w) { a = a + s_inc[w]; b = b + s_exc[w]; c += s_abs[w]; }
+    out->inc = a; out->exc = b; out->abs = c;
+  }
+}
+
 template <class Red>
 __device__ __forceinline__ void block_reduce_store(Red inc, Red exc, double asum, Partial<Red>* out) {
   __shared__ Red s_inc[32], s_exc[32];
