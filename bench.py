@@ -424,8 +424,11 @@ def batched_block(ctx, gbs, gi, n_req, n_err):
     t_single = time.perf_counter() - t0
     # the same batch certified to 1e-10 relative (AUTO: FP64, then fixed point, then triple-double)
     t0 = time.perf_counter()
-    cert = gbs.torontonian_batch(ctx, states, pats, "auto", "real", check=False)
+    cert, cert_status = gbs.torontonian_batch(ctx, states, pats, "auto", "real", check=False, return_status=True)
     t_cert = time.perf_counter() - t0
+    if cert_status not in (0, 4):  # GBS_OK, or GBS_EPRECISION with every value filled in
+        raise RuntimeError("certified batch failed with status %d: %s"
+                           % (cert_status, ctx.L.gbs_ctx_last_error(ctx.h).decode()))
     prec_counts = {}
     for c in cert:
         prec_counts[c.prec] = prec_counts.get(c.prec, 0) + 1
@@ -453,7 +456,8 @@ def batched_block(ctx, gbs, gi, n_req, n_err):
             "one_at_a_time_seconds": t_single, "one_at_a_time_requests_per_s": n_req / t_single,
             "speedup_vs_one_at_a_time": t_single / t_batch, "batch_gpu_launches": launches,
             "certified": {"seconds": t_cert, "requests_per_s": n_req / t_cert, "precisions": prec_counts,
-                          "max_rel_err_bound": worst_bound},
+                          "max_rel_err_bound": worst_bound, "status": cert_status,
+                          "above_1e-10": sum(1 for c in cert if c.p and c.err_bound > 1e-10 * abs(c.p))},
             "input_seconds": t_inputs, "fp32_error_study": err,
             "workload": "%d of the 4096 requests: N~U{8..22}, M~U{100,200,400}, r~U[0.4,1.0], "
                         "eta~U[0.25,1.0], Haar seeded per request; inputs built outside the timed "

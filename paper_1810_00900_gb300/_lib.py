@@ -323,8 +323,9 @@ def _prob(out: gbs_prob) -> "Prob":
 
 
 def torontonian_batch(ctx: Context, states, patterns, prec: str = "auto", basis: str = "auto",
-                      rel_tol: float = 0.0, check: bool = True):
-    """Click probabilities of many (state, pattern) requests in one batch."""
+                      rel_tol: float = 0.0, check: bool = True, return_status: bool = False):
+    """Click probabilities of many (state, pattern) requests in one batch (with return_status:
+    also the call's gbs_status, e.g. GBS_EPRECISION when some request stayed above rel_tol)."""
     n = len(patterns)
     if len(states) != n:
         raise ValueError("one state per pattern")
@@ -337,7 +338,8 @@ def torontonian_batch(ctx: Context, states, patterns, prec: str = "auto", basis:
                                      float(rel_tol), outs)
     if check:
         ctx.check(st)
-    return [_prob(outs[i]) for i in range(n)]
+    res = [_prob(outs[i]) for i in range(n)]
+    return (res, st) if return_status else res
 
 
 def sample(ctx: Context, st: State, n_samples: int, seed: int, N_post: int = 0, max_attempts: int = 1,

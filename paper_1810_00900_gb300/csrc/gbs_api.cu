@@ -203,6 +203,16 @@ gbs_status gbs_ctx_create(gbs_ctx** out, int device, size_t hbm_budget_bytes) {
   }
   ctx->own_stream = true;
   cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  {
+    // tree workspace of one batch: a quarter of the device (or half the budget)
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      total_b = (size_t)16 << 30;
+    }
+    ctx->batch_cap_bytes = total_b / 4;
+    if (hbm_budget_bytes) ctx->batch_cap_bytes = std::min(ctx->batch_cap_bytes, hbm_budget_bytes / 2);
+  }
   // Launch shapes before any autotuning: wider arithmetic makes the redundant
   // prefix elimination of the top kernel dearer, so it stops earlier.
   for (int b = 0; b < 2; ++b) {

@@ -242,6 +242,14 @@ gbs_status batch_eval(gbs_ctx* ctx, int prec, bool real, int ntrees, const Batch
                       const double* logdet, ProbOut* host_out) {
   if (ntrees <= 0) return GBS_OK;
   gbs_status st;
+  // too large for one plan: the two halves in turn (a tree's result does not depend
+  // on the rest of its batch, so the split changes no value)
+  auto split = [&]() -> gbs_status {
+    const int h = ntrees / 2;
+    gbs_status s2 = batch_eval(ctx, prec, real, h, trees, roots_dev, logdet, host_out);
+    if (s2) return s2;
+    return batch_eval(ctx, prec, real, ntrees - h, trees + h, roots_dev, logdet + h, host_out + h);
+  };
   const size_t n = (size_t)ntrees;
   auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t bytes = r256(n * sizeof(TreeOut)) + r256(n * sizeof(ProbOut)) + r256(n * sizeof(int));
@@ -256,7 +264,14 @@ gbs_status batch_eval(gbs_ctx* ctx, int prec, bool real, int ntrees, const Batch
   if ((st = stage(ctx, logdet, n * sizeof(double), &d_logdet)) || (st = stage(ctx, nm.data(), n * sizeof(int), &d_n)))
     return st;
   if ((st = check_cuda(ctx, cudaMemsetAsync(status, 0, n * sizeof(int), ctx->stream), "memset"))) return st;
-  if ((st = batch_variant(ctx, prec, real, ntrees, trees, roots_dev, outs, status))) return st;
+  ctx->batch_split = false;
+  if ((st = batch_variant(ctx, prec, real, ntrees, trees, roots_dev, outs, status))) {
+    if (st == GBS_ENOMEM && ctx->batch_split) {
+      ctx->batch_split = false;
+      return split();
+    }
+    return st;
+  }
   batch_finish_kernel<<<(ntrees + 127) / 128, 128, 0, ctx->stream>>>(
       outs, status, (const double*)d_logdet, (const int*)d_n, unit_roundoff_b(prec),
       err_factor(prec, 1) - err_factor(GBS_PREC_TD, 1), ntrees, po);

@@ -149,6 +149,12 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
   }
 
   // ---------------- memory
+  const size_t need = 2 * (size_t)region_total * sizeof(E) + 2 * (size_t)s_total * sizeof(S) +
+                      (size_t)(parts_total + chunks.size()) * sizeof(Partial<Red>);
+  if (ntrees > 1 && ctx->batch_cap_bytes && need > ctx->batch_cap_bytes) {
+    ctx->batch_split = true;  // the caller evaluates the batch in parts
+    return GBS_ENOMEM;
+  }
   gbs_status st;
   if ((st = dev_reserve(ctx, ctx->lvl[0], (size_t)region_total * sizeof(E))) ||
       (st = dev_reserve(ctx, ctx->lvl[1], (size_t)region_total * sizeof(E))) ||

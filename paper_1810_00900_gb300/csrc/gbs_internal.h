@@ -101,6 +101,12 @@ struct gbs_ctx {
 
   // request loop (see gbs_server.cu)
   void* server = nullptr;
+
+  // A batch whose tree workspace (level buffers, s values, partials) would
+  // exceed batch_cap_bytes is refused by the planner before anything is
+  // allocated or launched (batch_split set) and evaluated in parts instead.
+  size_t batch_cap_bytes = 0;
+  bool batch_split = false;
 };
 
 struct gbs_state {

@@ -200,6 +200,57 @@ __device__ __forceinline__ double rsqrt_f64(double x) {
   return ok ? y : __longlong_as_double(0x7ff8000000000000ll);
 }
 
+// 1/sqrt(x) for double x with no FP64 instruction at all: the FP32 seed of
+// rsqrt_f64, then the same third-order Newton-Raphson step in integer
+// arithmetic.  With x = M 2^(ex - 52) (M the 53-bit significand, ex = 2k + r)
+// and yf = my 2^(ey - 23):
+//   x' yf^2 = M my^2 2^-sh, sh = 98 - r - 2 ey, so D = 2^sh - M my^2 (a
+//   128-bit difference, exact) gives E = e 2^64 = floor(D 2^(64 - sh)),
+//   |E| < 2^45 (|e| < 2^-19);
+//   F = (e/2 + 3 e^2/8) 2^64 = E/2 + 3 (E^2 / 2^64) / 8;
+//   Y = my (2^64 + F), an 89-bit integer, rounded to 53 bits (half up) is the
+//   significand of y = Y 2^(ey - 87 - k).
+// Truncations of E and F cost at most a few units of 2^-64 and the dropped
+// 5 e^3/16 below 2^-55, so the result is within 0.51 ulp.  Non-positive,
+// subnormal, inf and NaN inputs give NaN.
+__device__ __forceinline__ double rsqrt_i64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const int eb = (int)(hi >> 20);  // sign and biased exponent (>= 0x800 for x < 0)
+  const bool ok = (unsigned)(eb - 1) < 0x7feu;
+  const int ex = eb - 1023;
+  const int r = ex & 1;
+  const int k = ex >> 1;
+  const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
+  const float xf = __uint_as_float(((unsigned)(127 + r) << 23) | ((hi & 0x000fffffu) << 3) | ((unsigned)b >> 29));
+  const unsigned yb = __float_as_uint(rsqrtf(xf));
+  const unsigned long long my = (yb & 0x7fffffu) | 0x800000u;
+  const int ey = (int)(yb >> 23) - 127;
+  const int sh = 98 - r - 2 * ey;  // in [96, 104] for any seed in (2^-3, 2)
+  const unsigned long long P = my * my;
+  const unsigned long long qlo = M * P, qhi = __umul64hi(M, P);
+  const unsigned long long dlo = 0ull - qlo;
+  const long long dhi = (long long)((1ull << (sh - 64)) - qhi - (qlo != 0ull));
+  const long long E = (long long)(((unsigned long long)dhi << (128 - sh)) + (dlo >> (sh - 64)));
+  const unsigned long long aE = (unsigned long long)(E < 0 ? -E : E);
+  const long long F = (E >> 1) + (long long)((3ull * __umul64hi(aE, aE)) >> 3);
+  const unsigned long long aF = (unsigned long long)(F < 0 ? -F : F);
+  const unsigned long long tlo = my * aF, thi = __umul64hi(my, aF);
+  unsigned long long ylo, yhi;
+  if (F >= 0) {
+    ylo = tlo;
+    yhi = my + thi;
+  } else {
+    ylo = 0ull - tlo;
+    yhi = my - thi - (tlo != 0ull);
+  }
+  const int lead = 127 - __clzll((long long)yhi);  // bit index of Y's leading one (86..88)
+  const int s = lead - 52;                          // 34..36
+  const unsigned long long m53 = ((yhi << (64 - s)) | (ylo >> s)) + ((ylo >> (s - 1)) & 1ull);
+  const long long bits = ((long long)(lead + ey - 87 - k + 1022) << 52) + (long long)m53;
+  return ok ? __longlong_as_double(bits) : __longlong_as_double(0x7ff8000000000000ll);
+}
+
 // -------------------------------------------------------- plain types -----
 GBS_HD double fms(double x, double a, double b) { return fma(-a, b, x); }
 GBS_HD double fpa(double x, double a, double b) { return fma(a, b, x); }
@@ -207,10 +258,12 @@ GBS_HD float fms(float x, float a, float b) { return fmaf(-a, b, x); }
 GBS_HD float fpa(float x, float a, float b) { return fmaf(a, b, x); }
 GBS_HD double to_double(double a) { return a; }
 GBS_HD double to_double(float a) { return (double)a; }
-#ifdef GBS_EXPERIMENT_CUDA_RSQRT
+#if defined(GBS_EXPERIMENT_CUDA_RSQRT)
 __device__ __forceinline__ double rsqrt_(double a) { return rsqrt(a); }
-#else
+#elif defined(GBS_EXPERIMENT_FMA_RSQRT)
 __device__ __forceinline__ double rsqrt_(double a) { return rsqrt_f64(a); }
+#else
+__device__ __forceinline__ double rsqrt_(double a) { return rsqrt_i64(a); }
 #endif
 __device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
 

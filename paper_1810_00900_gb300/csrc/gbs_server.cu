@@ -178,6 +178,17 @@ void worker_loop(Server* sv) {
   for (;;) {
     std::vector<Req*> probs, fresh;
     std::vector<Req*> active;
+    bool idle;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      idle = sv->active.empty();
+    }
+    if (idle) {
+      // nothing running: the stream is idle for want of work, not because the
+      // host is slow, so that time is no host gap
+      std::lock_guard<std::mutex> g(ctx->mu);
+      ctx->gap_open = false;
+    }
     {
       std::unique_lock<std::mutex> lk(sv->mu);
       sv->cv_work.wait_for(lk, std::chrono::milliseconds(20),

@@ -81,11 +81,12 @@ def test_graph_state_postselected_free_samples(ctx, eta):
 
 
 def test_free_sampling_48_modes(ctx):
+    # squeezing low enough that a chain ends with ~5 clicks: the oracle's subset sums stay small
     M = 48
     U = gi.haar_unitary(M, 44)
-    r = gi.uniform_range(44, "squeezing", M, 0.5, 1.0)
-    st = gbs.build_state(ctx, U, r, 0.8)
-    Sig = oracle.sigma(oracle.covariance(U, r, 0.8))
+    r = gi.uniform_range(44, "squeezing", M, 0.3, 0.6)
+    st = gbs.build_state(ctx, U, r, 0.7)
+    Sig = oracle.sigma(oracle.covariance(U, r, 0.7))
     n = 8
     pats, p0, stats, status = gbs.sample(ctx, st, n, seed=123, want_p0=True)
     assert status == 0 and stats["uncertified"] == 0
@@ -100,8 +101,8 @@ def test_free_sampling_48_modes(ctx):
             assert np.allclose(p0[i], np.array(ref["p0"]), rtol=0, atol=1e-10)
     assert stats["near_ties"] == near
     assert clicks >= 2 * n  # chains that click: the trees do grow along the way
-    # postselected on 6 clicks: early rejection along 48-step chains
-    n2, N_post, attempts = 4, 6, 30
+    # postselected on 3 clicks: early rejection along 48-step chains
+    n2, N_post, attempts = 4, 3, 30
     pats2, _, stats2, _ = gbs.sample(ctx, st, n2, seed=321, N_post=N_post, max_attempts=attempts)
     for i in range(n2):
         ref = oracle.sample_chain(Sig, 321, sample=i, N_post=N_post, max_attempts=attempts)
