@@ -253,7 +253,7 @@ __device__ __forceinline__ void pair_group(const double (&c)[sym(D)], double s, 
   const double u00 = c[tri(OFF + 2, OFF)], u01 = c[tri(OFF + 2, OFF + 1)];
   const double u10 = c[tri(OFF + 3, OFF)], u11 = c[tri(OFF + 3, OFF + 1)];
   const double da = fma(a00, a11, -a01 * a01);
-  const double ga = rsqrt_f64(da);
+  const double ga = rsqrt_(da);
   const double inv = ga * ga;
   const double q00 = a00 * inv, q11 = a11 * inv, m = -a01 * inv;
   // rows of B P_a^-1, then D = B P_a^-1 B^T
@@ -265,7 +265,7 @@ __device__ __forceinline__ void pair_group(const double (&c)[sym(D)], double s, 
   const double c00 = b00 - d00, c11 = b11 - d11, c01 = b01 - d01;
   const double db = fma(b00, b11, -b01 * b01);
   const double dc = fma(c00, c11, -c01 * c01);
-  const double gb = rsqrt_f64(db), gc = rsqrt_f64(dc);
+  const double gb = rsqrt_(db), gc = rsqrt_(dc);
   const double ha = pair_hm1(a00, a11, a01, da, ga);
   const double hc = pair_hm1(c00, c11, c01, dc, gc);
   const double delta = fma(d00, d11, -d01 * d01) - fma(b11, d00, fma(b00, d11, -2.0 * b01 * d01));
@@ -285,7 +285,7 @@ template <int D, int OFF, bool NEG>
 __device__ __forceinline__ void pair_single(const double (&c)[sym(D)], double s, Sums<double>& acc) {
   const double p00 = c[tri(OFF, OFF)], p11 = c[tri(OFF + 1, OFF + 1)], p01 = c[tri(OFF + 1, OFF)];
   const double det = fma(p00, p11, -p01 * p01);
-  const double g = rsqrt_f64(det);
+  const double g = rsqrt_(det);
   const double h = pair_hm1(p00, p11, p01, det, g);
   if (NEG) acc.ip = fma(-s, h, acc.ip); else acc.ip = fma(s, h, acc.ip);
   acc.ep = fma(s, fabs(h) + g, acc.ep);
