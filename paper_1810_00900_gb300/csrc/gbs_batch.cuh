@@ -116,6 +116,56 @@ __device__ __forceinline__ void smem_expand(E*& src, E*& dst, typename scale_of<
   typedef typename real_of<E>::type T;
   typedef typename scale_of<E>::type S;
   const int nthr = blockDim.x;
+  if constexpr (std::is_same<E, double>::value && !kExperimentAdjugate) {
+    // FP64 real basis: the pivot block of node t factored as P = R R^T
+    // (r0 = p00^-1/2, w = p10 r0, r1 = (p11 - w^2)^-1/2, det(P)^-1/2 = r0 r1), the
+    // rows of W = U R^-T written over the pivot columns they come from (dead after
+    // the split), then C' = C - W W^T one lower-triangle entry per task, so every
+    // thread has the same work (two FMAs per entry).  A pivot that is not
+    // positive definite makes r0 or r1 NaN, which reaches every term below it.
+    for (int lvl = 0; lvl < levels; ++lvl) {
+      for (int t = threadIdx.x; t < nodes; t += nthr) {
+        const double p00 = src[tri(0, 0) * nodes + t], p11 = src[tri(1, 1) * nodes + t];
+        const double p10 = src[tri(1, 0) * nodes + t];
+        const double r0 = rsqrt_(p00);
+        const double w = p10 * r0;
+        const double r1 = rsqrt_(fma(-w, w, p11));
+        const double g = r0 * r1;
+        pq00[t] = r0;
+        pq11[t] = r1;
+        pm10[t] = -w * g;
+        sdst[2 * t] = ssrc[t];
+        sdst[2 * t + 1] = ssrc[t] * g;
+      }
+      __syncthreads();
+      const int rows = 2 * q - 2;
+      for (int task = threadIdx.x; task < nodes * rows; task += nthr) {
+        const int t = task % nodes, a = task / nodes;
+        double* r = src + tri(a + 2, 0) * nodes + t;  // (a+2, 0) and, one entry on, (a+2, 1)
+        const double u0 = r[0], u1 = r[nodes];
+        r[0] = u0 * pq00[t];
+        r[nodes] = fma(u0, pm10[t], u1 * pq11[t]);
+      }
+      __syncthreads();
+      const int n2 = 2 * nodes;
+      for (int task = threadIdx.x; task < nodes * sym(rows); task += nthr) {
+        const int t = task % nodes, e = task / nodes;
+        int a, b;
+        untri(e, a, b);
+        const double x = src[tri(a + 2, b + 2) * nodes + t];
+        const double w0a = src[tri(a + 2, 0) * nodes + t], w1a = src[tri(a + 2, 1) * nodes + t];
+        const double w0b = src[tri(b + 2, 0) * nodes + t], w1b = src[tri(b + 2, 1) * nodes + t];
+        dst[e * n2 + 2 * t] = x;
+        dst[e * n2 + 2 * t + 1] = fma(-w1a, w1b, fma(-w0a, w0b, x));
+      }
+      __syncthreads();
+      E* tmp = src; src = dst; dst = tmp;
+      S* ts = ssrc; ssrc = sdst; sdst = ts;
+      nodes = n2;
+      --q;
+    }
+    return;
+  }
   for (int lvl = 0; lvl < levels; ++lvl) {
     for (int t = threadIdx.x; t < nodes; t += nthr) {
       const T p00 = re_of(src[tri(0, 0) * nodes + t]);
@@ -362,15 +412,16 @@ __global__ void __launch_bounds__(128, leaf_min_blocks<E>::value) batch_leaf_ker
 }
 
 // -------------------------------------------------------------- subtree --
-// One CTA per node with q_root undecided modes: breadth-first expansion of the
-// first e_levels levels in shared memory (two ping-pong level buffers, node
-// matrices entry-major), then one thread per resulting node runs the register
+// One CTA per k_roots consecutive nodes with q_root undecided modes (of one
+// tree): breadth-first expansion of the first e_levels levels of all of them
+// together in shared memory (two ping-pong level buffers, node matrices
+// entry-major), then one thread per resulting node runs the register
 // depth-first subtree of the last Q levels.  One partial per CTA.
 struct SubSeg {
   long long block_begin;  // first CTA of this tree
-  long long count;        // CTA roots of this tree
+  long long count;        // subtree roots of this tree
   long long base, s_base; // where the roots are (level buffer `buf`)
-  int q_root, e_levels, depth_leaf, tree, buf, pad;
+  int q_root, e_levels, depth_leaf, tree, buf, k_roots;
 };
 
 template <class E, int Q, bool PAIR = false>
@@ -394,17 +445,21 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
   T* pq11 = pq00 + nthr;
   for (long long vb = blockIdx.x; vb < total_blocks; vb += gridDim.x) {
     const SubSeg sg = segs[find_seg(segs, nseg, vb, &SubSeg::block_begin)];
-    const long long root = vb - sg.block_begin;
+    const long long root = (vb - sg.block_begin) * sg.k_roots;  // first root of this CTA
+    const int nroots = (int)min((long long)sg.k_roots, sg.count - root);
     const E* rsrc = (sg.buf ? buf1 : buf0) + sg.base;
     int q = sg.q_root;
-    for (int e = threadIdx.x; e < sym(2 * q); e += nthr) bufA[e] = ld_node(rsrc, e, sg.count, root);
-    if (threadIdx.x == 0) sA[0] = (sg.buf ? s1 : s0)[sg.s_base + root];
+    for (int i = threadIdx.x; i < sym(2 * q) * nroots; i += nthr) {
+      const int e = i / nroots, k = i - e * nroots;
+      bufA[i] = ld_node(rsrc, e, sg.count, root + k);
+    }
+    for (int k = threadIdx.x; k < nroots; k += nthr) sA[k] = (sg.buf ? s1 : s0)[sg.s_base + root + k];
     __syncthreads();
     E* src = bufA;
     E* dst = bufB;
     S* ssrc = sA;
     S* sdst = sB;
-    int nodes = 1;
+    int nodes = nroots;
     bool bad = false;
     smem_expand<E>(src, dst, ssrc, sdst, pm10, pq00, pq11, nodes, q, sg.e_levels, bad);
     if (bad) atomicExch(status + sg.tree, bad_status<typename real_of<E>::type>());
@@ -417,7 +472,7 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
         for (int e = 0; e < sym(2 * Q); ++e) c[e] = src[e * nodes + t];
         const bool ok = subtree_run<E, Q, PAIR>(c, ssrc[t], a);
         if (!ok || !isfinite((a.ip + a.in) + (a.ep + a.en))) atomicExch(status + sg.tree, bad_status<T>());
-        const unsigned long long gnode = ((unsigned long long)root << sg.e_levels) | (unsigned long long)t;
+        const unsigned long long gnode = ((unsigned long long)root << sg.e_levels) + (unsigned long long)t;
         if ((sg.depth_leaf - __popcll(gnode)) & 1) {
           const double t0 = a.ip, t1 = a.ep;
           a.ip = a.in; a.in = t0; a.ep = a.en; a.en = t1;
@@ -433,7 +488,7 @@ __global__ void __launch_bounds__(128) batch_subtree_kernel(
         for (int e = 0; e < sym(2 * Q); ++e) c[e] = src[e * nodes + t];
         const S sv = ssrc[t];
         if (!subtree_sums<E, Q, PAIR>(c, sv, inc, exc, asum)) atomicExch(status + sg.tree, bad_status<T>());
-        const unsigned long long gnode = ((unsigned long long)root << sg.e_levels) | (unsigned long long)t;
+        const unsigned long long gnode = ((unsigned long long)root << sg.e_levels) + (unsigned long long)t;
         if ((sg.depth_leaf - __popcll(gnode)) & 1) {
           inc = red_neg(inc);
           exc = red_neg(exc);

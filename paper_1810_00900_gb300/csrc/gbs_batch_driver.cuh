@@ -103,7 +103,9 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
     }
   }
   // leaf (sub_e == 0) or subtree segments, grouped by Q (one launch per distinct Q)
-  const int nthr = sub_e > 0 ? (1 << sub_e) : 128;
+  // subtree CTAs have 2^sub_e threads, at least one warp; a CTA expands K = nthr / 2^el
+  // consecutive roots of one tree together (el: the levels its roots expand)
+  const int nthr = sub_e > 0 ? (1 << std::max(sub_e, 5)) : 128;
   std::vector<std::vector<LeafSeg>> leaf(QMAX + 1);
   std::vector<std::vector<SubSeg>> subs(QMAX + 1);
   std::vector<long long> grp_blocks(QMAX + 1, 0);
@@ -115,14 +117,16 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
       const long long count = 1LL << depth[t];
       if (sub_e > 0) {
         const int el = qroot[t] - Q[t];
+        const int K = nthr >> el;
+        const long long nb = (count + K - 1) / K;
         subs[qv].push_back(SubSeg{grp_blocks[qv], count, region[t], sreg[t], qroot[t], el, trees[t].n - Q[t], t,
-                                  depth[t] & 1, 0});
+                                  depth[t] & 1, K});
         for (int j = 0; j <= el; ++j) {
-          const int c = (1 << j) * sym(2 * (qroot[t] - j));
+          const int c = K * (1 << j) * sym(2 * (qroot[t] - j));
           if (j & 1) capB = std::max(capB, c); else capA = std::max(capA, c);
         }
-        ranges[t] = PartRange{grp_blocks[qv], count};
-        grp_blocks[qv] += count;
+        ranges[t] = PartRange{grp_blocks[qv], nb};
+        grp_blocks[qv] += nb;
       } else {
         const long long nb = (count + 127) / 128;
         leaf[qv].push_back(LeafSeg{grp_blocks[qv], count, region[t], sreg[t], depth[t], t, depth[t] & 1, 0});

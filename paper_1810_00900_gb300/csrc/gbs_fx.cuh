@@ -350,6 +350,11 @@ __device__ __forceinline__ fxn<L, F> rsqrt_(const fxn<L, F>& x) {
 }
 
 // ------------------------------------------------------ sums and reduction --
+// The four sign-split sums are exact and non-negative: add them, convert once.
+template <int L, int F>
+struct sums_total<fxn<L, F>> {
+  static GBS_HD double of(const Sums<fxn<L, F>>& a) { return to_double((a.ip + a.in) + (a.ep + a.en)); }
+};
 template <> struct acc_traits<fxn4> { typedef fxn4s Acc; typedef fxn4s Red; };
 template <> struct acc_traits<fx> { typedef fxs Acc; typedef fxs Red; };
 template <> struct acc_traits<fxw> { typedef fxws Acc; typedef fxws Red; };

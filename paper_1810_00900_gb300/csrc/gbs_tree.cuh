@@ -100,6 +100,14 @@ template <class Acc>
 struct Sums {
   Acc ip, in, ep, en;
 };
+// Sum of |terms| of a thread's sign-split sums as a double (specialised where the
+// sums are exact integers: add first, convert once).
+template <class Acc>
+struct sums_total {
+  static GBS_HD double of(const Sums<Acc>& a) {
+    return to_double(a.ip) + to_double(a.in) + (to_double(a.ep) + to_double(a.en));
+  }
+};
 template <class Acc>
 GBS_HD Sums<Acc> sums_zero() {
   const Acc z = from_double<Acc>(0.0);
@@ -319,7 +327,11 @@ struct Dfs {
       // costs two fused multiply-adds.  A one-mode node needs only det(P).
       const double p00 = c[tri(OFF, OFF)], p11 = c[tri(OFF + 1, OFF + 1)], p10 = c[tri(OFF + 1, OFF)];
       if constexpr (Q == 1) {
+#if defined(GBS_EXPERIMENT_CUDA_RSQRT) || defined(GBS_EXPERIMENT_FMA_RSQRT) || defined(GBS_EXPERIMENT_FP64_DET)
         const double g = rsqrt_(fma(p00, p11, -p10 * p10));
+#else
+        const double g = rsqrt_det2_i64(p00, p11, p10);  // det and its inverse square root on the integer pipes
+#endif
         if (NEG) { acc.in = fma(s, g, acc.in); acc.ep += s; } else { acc.ip = fma(s, g, acc.ip); acc.en += s; }
       } else {
         constexpr int DN = 2 * Q - 2;
@@ -408,7 +420,7 @@ __device__ __forceinline__ bool subtree_sums(const E (&c)[sym(2 * Q)], const typ
   } else {
     inc = red_diff(a.ip, a.in, (Red*)nullptr);
     exc = red_diff(a.ep, a.en, (Red*)nullptr);
-    asum = to_double(a.ip) + to_double(a.in) + (to_double(a.ep) + to_double(a.en));
+    asum = sums_total<Acc>::of(a);
     return !bad && isfinite(asum);
   }
 }
