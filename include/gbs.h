@@ -314,10 +314,11 @@ gbs_status gbs_poll(gbs_ctx* ctx, uint64_t ticket, gbs_result* out, int64_t time
 gbs_status gbs_server_stats_get(gbs_ctx* ctx, gbs_server_stats* out);
 
 /* Launch shape of the batched enumeration, per (precision, basis):
- *   sub_e          0, or 5..7: levels each subtree CTA (2^sub_e threads, at
- *                  least one warp) expands in shared memory before its threads
- *                  run the register depth-first leaves (0 = no in-CTA
- *                  expansion, one thread per leaf root);
+ *   sub_e          0..7: levels a subtree CTA (2^sub_e threads, at least one
+ *                  warp, so 32 >> sub_e roots at once below 5) expands in
+ *                  shared memory before its threads run the register
+ *                  depth-first leaves (0 = no in-CTA expansion, one thread per
+ *                  leaf root);
  *   d_top          prefix depth the first kernel reaches by eliminating each
  *                  node's included prefix modes in shared memory;
  *   grid_per_sm    0 = one CTA per work unit; k > 0 = persistent grid of k CTAs

@@ -116,56 +116,6 @@ __device__ __forceinline__ void smem_expand(E*& src, E*& dst, typename scale_of<
   typedef typename real_of<E>::type T;
   typedef typename scale_of<E>::type S;
   const int nthr = blockDim.x;
-  if constexpr (std::is_same<E, double>::value && !kExperimentAdjugate) {
-    // FP64 real basis: the pivot block of node t factored as P = R R^T
-    // (r0 = p00^-1/2, w = p10 r0, r1 = (p11 - w^2)^-1/2, det(P)^-1/2 = r0 r1), the
-    // rows of W = U R^-T written over the pivot columns they come from (dead after
-    // the split), then C' = C - W W^T one lower-triangle entry per task, so every
-    // thread has the same work (two FMAs per entry).  A pivot that is not
-    // positive definite makes r0 or r1 NaN, which reaches every term below it.
-    for (int lvl = 0; lvl < levels; ++lvl) {
-      for (int t = threadIdx.x; t < nodes; t += nthr) {
-        const double p00 = src[tri(0, 0) * nodes + t], p11 = src[tri(1, 1) * nodes + t];
-        const double p10 = src[tri(1, 0) * nodes + t];
-        const double r0 = rsqrt_(p00);
-        const double w = p10 * r0;
-        const double r1 = rsqrt_(fma(-w, w, p11));
-        const double g = r0 * r1;
-        pq00[t] = r0;
-        pq11[t] = r1;
-        pm10[t] = -w * g;
-        sdst[2 * t] = ssrc[t];
-        sdst[2 * t + 1] = ssrc[t] * g;
-      }
-      __syncthreads();
-      const int rows = 2 * q - 2;
-      for (int task = threadIdx.x; task < nodes * rows; task += nthr) {
-        const int t = task % nodes, a = task / nodes;
-        double* r = src + tri(a + 2, 0) * nodes + t;  // (a+2, 0) and, one entry on, (a+2, 1)
-        const double u0 = r[0], u1 = r[nodes];
-        r[0] = u0 * pq00[t];
-        r[nodes] = fma(u0, pm10[t], u1 * pq11[t]);
-      }
-      __syncthreads();
-      const int n2 = 2 * nodes;
-      for (int task = threadIdx.x; task < nodes * sym(rows); task += nthr) {
-        const int t = task % nodes, e = task / nodes;
-        int a, b;
-        untri(e, a, b);
-        const double x = src[tri(a + 2, b + 2) * nodes + t];
-        const double w0a = src[tri(a + 2, 0) * nodes + t], w1a = src[tri(a + 2, 1) * nodes + t];
-        const double w0b = src[tri(b + 2, 0) * nodes + t], w1b = src[tri(b + 2, 1) * nodes + t];
-        dst[e * n2 + 2 * t] = x;
-        dst[e * n2 + 2 * t + 1] = fma(-w1a, w1b, fma(-w0a, w0b, x));
-      }
-      __syncthreads();
-      E* tmp = src; src = dst; dst = tmp;
-      S* ts = ssrc; ssrc = sdst; sdst = ts;
-      nodes = n2;
-      --q;
-    }
-    return;
-  }
   for (int lvl = 0; lvl < levels; ++lvl) {
     for (int t = threadIdx.x; t < nodes; t += nthr) {
       const T p00 = re_of(src[tri(0, 0) * nodes + t]);

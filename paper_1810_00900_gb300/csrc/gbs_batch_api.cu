@@ -515,7 +515,7 @@ extern "C" gbs_status gbs_autotune(gbs_ctx* ctx, int prec, int basis, int n, int
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int subs[] = {0, 5, 6, 7};
+  const int subs[] = {0, 2, 3, 4, 5, 6, 7};
   const int tops[] = {6, 8, 9, 10};
   const int grids[] = {0, 8};
   const long long lts[] = {1LL << 17, 1LL << 19};
@@ -587,7 +587,7 @@ extern "C" gbs_status gbs_get_tuning(gbs_ctx* ctx, int prec, int basis, int* sub
 extern "C" gbs_status gbs_set_tuning(gbs_ctx* ctx, int prec, int basis, int sub_e, int d_top, int grid_per_sm,
                                      long long level_threads, int q_drop, int mid_e) {
   if (!ctx || prec < GBS_PREC_FP64 || prec > kPrecLast || sub_e < 0 || sub_e > 7 ||
-      (sub_e > 0 && sub_e < 5) || d_top < 0 ||
+      d_top < 0 ||
       d_top > 16 || grid_per_sm < 0 || level_threads < 1 || q_drop < 0 || q_drop > 2 || mid_e < 0 || mid_e > 8)
     return GBS_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);

@@ -200,81 +200,55 @@ __device__ __forceinline__ double rsqrt_f64(double x) {
   return ok ? y : __longlong_as_double(0x7ff8000000000000ll);
 }
 
-// Inverse square roots with no FP64 instruction at all: the FP32 seed of
+// 1/sqrt(x) for double x with no FP64 instruction at all: the FP32 seed of
 // rsqrt_f64, then the same third-order Newton-Raphson step in integer
-// arithmetic.  For v = Mn 2^(ex - 63) (Mn a 64-bit significand, top bit set,
-// ex = 2k + r) and the seed yf = my 2^(ey - 23):
-//   v' yf^2 = Mn my^2 2^-sh, sh = 109 - r - 2 ey, so D = 2^sh - Mn my^2 (exact,
-//   128 bits) gives E = e 2^64 = floor(D 2^(64 - sh)), |E| < 2^45;
+// arithmetic.  With x = M 2^(ex - 52) (M the 53-bit significand, ex = 2k + r)
+// and yf = my 2^(ey - 23):
+//   x' yf^2 = M my^2 2^-sh, sh = 98 - r - 2 ey, so D = 2^sh - M my^2 (a
+//   128-bit difference, exact) gives E = e 2^64 = floor(D 2^(64 - sh)),
+//   |E| < 2^45 (|e| < 2^-19);
 //   F = (e/2 + 3 e^2/8) 2^64 = E/2 + 3 (E^2 / 2^64) / 8;
 //   Y = my (2^64 + F), an 89-bit integer, rounded to 53 bits (half up) is the
-//   significand of the result Y 2^(ey - 87 - k).
-// Truncations of E and F cost a few units of 2^-64 and the dropped 5 e^3/16
-// stays below 2^-55, so the result is within 0.51 ulp of v^(-1/2).
-__device__ __forceinline__ double rsqrt_core_i64(unsigned long long Mn, int ex) {
+//   significand of y = Y 2^(ey - 87 - k).
+// Truncations of E and F cost at most a few units of 2^-64 and the dropped
+// 5 e^3/16 below 2^-55, so the result is within 0.51 ulp.  Non-positive,
+// subnormal, inf and NaN inputs give NaN.
+__device__ __forceinline__ double rsqrt_i64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const int eb = (int)(hi >> 20);  // sign and biased exponent (>= 0x800 for x < 0)
+  const bool ok = (unsigned)(eb - 1) < 0x7feu;
+  const int ex = eb - 1023;
   const int r = ex & 1;
-  const int k = ex >> 1;  // floor(ex / 2)
-  const float xf = __uint_as_float(((unsigned)(127 + r) << 23) | (unsigned)((Mn >> 40) & 0x7fffffu));
+  const int k = ex >> 1;
+  const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
+  const float xf = __uint_as_float(((unsigned)(127 + r) << 23) | ((hi & 0x000fffffu) << 3) | ((unsigned)b >> 29));
   const unsigned yb = __float_as_uint(rsqrtf(xf));
   const unsigned long long my = (yb & 0x7fffffu) | 0x800000u;
   const int ey = (int)(yb >> 23) - 127;
-  const int sh = 109 - r - 2 * ey;  // in [107, 115] for any seed in (2^-3, 2)
-  const __int128 D = ((__int128)1 << sh) - (__int128)((unsigned __int128)Mn * (my * my));
-  const long long E = (long long)(D >> (sh - 64));
+  const int sh = 98 - r - 2 * ey;  // in [96, 104] for any seed in (2^-3, 2)
+  const unsigned long long P = my * my;
+  const unsigned long long qlo = M * P, qhi = __umul64hi(M, P);
+  const unsigned long long dlo = 0ull - qlo;
+  const long long dhi = (long long)((1ull << (sh - 64)) - qhi - (qlo != 0ull));
+  const long long E = (long long)(((unsigned long long)dhi << (128 - sh)) + (dlo >> (sh - 64)));
   const unsigned long long aE = (unsigned long long)(E < 0 ? -E : E);
   const long long F = (E >> 1) + (long long)((3ull * __umul64hi(aE, aE)) >> 3);
-  const unsigned __int128 Y = ((unsigned __int128)my << 64) + (unsigned __int128)((__int128)(long long)my * F);
-  const unsigned long long yhi = (unsigned long long)(Y >> 64);
-  const int lead = 127 - __clzll((long long)yhi);  // 86..88
-  const int sft = lead - 52;
-  const unsigned long long m53 = (unsigned long long)(Y >> sft) + (unsigned long long)((Y >> (sft - 1)) & 1u);
-  return __longlong_as_double(((long long)(lead + ey - 87 - k + 1022) << 52) + (long long)m53);
-}
-
-// 1/sqrt(x) of a double x (0.51 ulp, integer pipes only); x that is not a
-// positive normal double (zero, negative, subnormal, inf, NaN) gives NaN.
-__device__ __forceinline__ double rsqrt_i64(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int eb = (int)(b >> 52);  // sign and biased exponent
-  const bool ok = (unsigned)(eb - 1) < 0x7feu;
-  const double y = rsqrt_core_i64(((b << 11) | (1ull << 63)), eb - 1023);
-  return ok ? y : __longlong_as_double(0x7ff8000000000000ll);
-}
-
-// det(P)^(-1/2) = (p00 p11 - p10^2)^(-1/2) of a 2 x 2 pivot block, integer
-// pipes only: the two products are exact 106-bit integers, the difference is
-// exact (p10^2 truncated only where it lies below the last bit of p00 p11),
-// and its leading 64 bits feed rsqrt_core_i64, so the result is within about
-// 0.51 ulp of the exact determinant's inverse square root (an FP64 det loses
-// accuracy to cancellation first).  A block that is not positive definite
-// (p00 <= 0, p11 <= 0, det <= 0), or an entry that is not a normal double,
-// gives NaN.
-__device__ __forceinline__ double rsqrt_det2_i64(double p00, double p11, double p10) {
-  const unsigned long long b0 = (unsigned long long)__double_as_longlong(p00);
-  const unsigned long long b1 = (unsigned long long)__double_as_longlong(p11);
-  const unsigned long long b2 = (unsigned long long)__double_as_longlong(p10) & 0x7fffffffffffffffull;
-  const int e0 = (int)(b0 >> 52), e1 = (int)(b1 >> 52), e2 = (int)(b2 >> 52);
-  bool ok = (unsigned)(e0 - 1) < 0x7feu && (unsigned)(e1 - 1) < 0x7feu && e2 < 0x7ff;
-  const unsigned long long m0 = (b0 & 0xfffffffffffffull) | (1ull << 52);
-  const unsigned long long m1 = (b1 & 0xfffffffffffffull) | (1ull << 52);
-  const unsigned long long m2 = e2 ? ((b2 & 0xfffffffffffffull) | (1ull << 52)) : 0ull;  // |p10| < 2^-1022: 0
-  const unsigned __int128 A = (unsigned __int128)m0 * m1;  // p00 p11 = A 2^(e0 + e1 - 2150)
-  const unsigned __int128 B = (unsigned __int128)m2 * m2;  // p10^2 = B 2^(2 e2 - 2150)
-  const int d = e0 + e1 - 2 * e2;
-  unsigned __int128 Bs;
-  if (d >= 0) {
-    Bs = d < 128 ? (B >> d) : (unsigned __int128)0;
+  const unsigned long long aF = (unsigned long long)(F < 0 ? -F : F);
+  const unsigned long long tlo = my * aF, thi = __umul64hi(my, aF);
+  unsigned long long ylo, yhi;
+  if (F >= 0) {
+    ylo = tlo;
+    yhi = my + thi;
   } else {
-    ok = ok && -d < 22;  // otherwise p10^2 > p00 p11
-    Bs = B << ((-d) & 127);
+    ylo = 0ull - tlo;
+    yhi = my - thi - (tlo != 0ull);
   }
-  const unsigned __int128 Dv = A - Bs;  // det = Dv 2^(e0 + e1 - 2150)
-  ok = ok && A > Bs;
-  const unsigned long long dhi = (unsigned long long)(Dv >> 64), dlo = (unsigned long long)Dv;
-  const int lz = dhi ? __clzll((long long)dhi) : 64 + __clzll((long long)(dlo | 1ull));
-  const unsigned long long Mn = (unsigned long long)((Dv << (lz & 127)) >> 64);
-  const double y = rsqrt_core_i64(Mn, 127 - lz + e0 + e1 - 2150);
-  return ok ? y : __longlong_as_double(0x7ff8000000000000ll);
+  const int lead = 127 - __clzll((long long)yhi);  // bit index of Y's leading one (86..88)
+  const int s = lead - 52;                          // 34..36
+  const unsigned long long m53 = ((yhi << (64 - s)) | (ylo >> s)) + ((ylo >> (s - 1)) & 1ull);
+  const long long bits = ((long long)(lead + ey - 87 - k + 1022) << 52) + (long long)m53;
+  return ok ? __longlong_as_double(bits) : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 // -------------------------------------------------------- plain types -----

@@ -327,11 +327,7 @@ struct Dfs {
       // costs two fused multiply-adds.  A one-mode node needs only det(P).
       const double p00 = c[tri(OFF, OFF)], p11 = c[tri(OFF + 1, OFF + 1)], p10 = c[tri(OFF + 1, OFF)];
       if constexpr (Q == 1) {
-#if defined(GBS_EXPERIMENT_CUDA_RSQRT) || defined(GBS_EXPERIMENT_FMA_RSQRT) || defined(GBS_EXPERIMENT_FP64_DET)
         const double g = rsqrt_(fma(p00, p11, -p10 * p10));
-#else
-        const double g = rsqrt_det2_i64(p00, p11, p10);  // det and its inverse square root on the integer pipes
-#endif
         if (NEG) { acc.in = fma(s, g, acc.in); acc.ep += s; } else { acc.ip = fma(s, g, acc.ip); acc.en += s; }
       } else {
         constexpr int DN = 2 * Q - 2;

@@ -25,7 +25,7 @@ def test_launch_shapes_agree(ctx):
     H = real_basis_block(oracle.sigma_inv_block(Sig, gi.random_modes(150, 17, seed=9)))
     ref, ref_abs = oracle_tor(H)
     seen = []
-    for sub_e in (0, 5, 6, 7):
+    for sub_e in (0, 2, 3, 5, 6, 7):  # below 5: one-warp CTAs expanding several roots at once
         for d_top in (0, 4, 10):
             for grid in (0, 2):
                 for q_drop, mid_e in ((0, 0), (1, 0), (0, 5), (1, 3)):
@@ -37,7 +37,7 @@ def test_launch_shapes_agree(ctx):
     ctx.set_tuning("dd", "real", 5, 10, 0, 1 << 18)
     # the fixed-point sums are exact and their reduction order fixed: every shape gives the same bits
     fx_seen = set()
-    for sub_e in (0, 6):
+    for sub_e in (0, 2, 4, 6):
         for d_top in (0, 8):
             for q_drop, mid_e in ((0, 0), (1, 0), (2, 0), (0, 5), (1, 2)):
                 ctx.set_tuning("fx", "real", sub_e, d_top, 8, 1 << 17, q_drop, mid_e)
@@ -46,6 +46,12 @@ def test_launch_shapes_agree(ctx):
                 assert abs(float(frac3(tor) - ref.to_fraction())) <= 8 * 17 * 2.0 ** -140 * ref_abs
     assert len(fx_seen) == 1
     ctx.set_tuning("fx", "real", 6, 6, 0, 1 << 18)
+    # FP64 with several roots per shared-memory CTA: within the FP64 bound of the same input
+    for sub_e in (1, 2, 3, 4):
+        ctx.set_tuning("fp64", "real", sub_e, 6, 8, 1 << 17, 0, 4)
+        _, _, tor, a = gbs.subset_sum(ctx, H, "real", "fp64")
+        assert abs(float(frac3(tor) - ref.to_fraction())) <= 8 * 17 * 2.0 ** -53 * ref_abs + 24 * 2.0 ** -53 * a
+    ctx.set_tuning("fp64", "real", 5, 8, 8, 1 << 17, 0, 4)
 
 
 def test_autotune_picks_a_candidate(ctx):

@@ -3,8 +3,8 @@
 The FP64 kernels form every det(P)^(-1/2) without FP64 instructions (an FP32 seed and one exact
 integer Newton step, accurate to about 0.51 units in the last place).  Two trees expose them:
 
-* one mode, G = P (2 x 2): the tree's included sum is exactly det(P)^(-1/2), det formed in
-  integer arithmetic from the three entries;
+* one mode, G = P (2 x 2): the tree's included sum is exactly d^(-1/2), with d the FP64
+  determinant fma(p00, p11, -fl(p10^2));
 * two modes, G = diag(P_a, I) with P_a = diag(x, 1): the pivot of mode a is factored as
   r0 = x^(-1/2), r1 = 1, and the included sum is exactly r0 - 1.
 
@@ -65,8 +65,8 @@ def test_leaf_determinant_inverse_square_root(ctx):
         inc, exc, _, _ = gbs.subset_sum(ctx, G, "real", "fp64")
         g = frac3(inc)
         assert frac3(exc) == -1
-        det = Fraction(p00) * Fraction(p11) - Fraction(p10) ** 2
-        check(float(g), inv_sqrt_exact(det), (p00, p11, p10))
+        det = float(Fraction(p00) * Fraction(p11) - Fraction(p10 * p10))  # one rounding, as the FMA
+        check(float(g), inv_sqrt_exact(Fraction(det)), (p00, p11, p10))
         assert g == Fraction(float(g))  # a single double
 
 
