@@ -399,12 +399,16 @@ def walltime_block(ctx, gbs, gi, ms):
                         "run together, time per sample)"}
 
 
-def batched_block(ctx, gbs, gi, n_req, n_err):
+def batched_block(ctx, gbs, gi, n_req, n_err, autotune=True):
     """Uneven probability requests (N ~ U{8..22}, M ~ U{100, 200, 400}, r ~ U[0.4, 1.0],
     eta ~ U[0.25, 1.0], Haar unitary seeded per request) evaluated as one batch in FP64 and
     one at a time; plus the FP32 / FP64 / paired-FP64 error study on a subsample against certified
     values."""
     reqs = gi.batched_requests(4096)[:n_req]
+    if autotune:
+        # launch shapes for a batch of uneven trees like this one (22 .. 8 modes), not the single
+        # 24-mode tree of the headline
+        ctx.autotune("fp64", "real", 22, n_trees=15)
     t0 = time.perf_counter()
     Us = haar_unitaries([(q.M, q.seed) for q in reqs])
     states = [gbs.build_state(ctx, U, np.full(q.M, q.r), q.eta) for U, q in zip(Us, reqs)]
@@ -455,6 +459,7 @@ def batched_block(ctx, gbs, gi, n_req, n_err):
             "batch_seconds": t_batch, "batch_requests_per_s": n_req / t_batch, "batch_terms_per_s": terms / t_batch,
             "one_at_a_time_seconds": t_single, "one_at_a_time_requests_per_s": n_req / t_single,
             "speedup_vs_one_at_a_time": t_single / t_batch, "batch_gpu_launches": launches,
+            "fp64_tuning": ctx.tuning("fp64", "real"),
             "certified": {"seconds": t_cert, "requests_per_s": n_req / t_cert, "precisions": prec_counts,
                           "max_rel_err_bound": worst_bound, "status": cert_status,
                           "above_1e-10": sum(1 for c in cert if c.p and c.err_bound > 1e-10 * abs(c.p))},
@@ -825,7 +830,7 @@ def main():
     if args.sampler_traj > 0:
         line["sampler"] = sampler_block(ctx, gbs, gi, args.sampler_traj, ws, local, autotune=not args.no_autotune)
     if args.batched_req > 0:
-        line["batched"] = batched_block(ctx, gbs, gi, args.batched_req, 48)
+        line["batched"] = batched_block(ctx, gbs, gi, args.batched_req, 48, autotune=not args.no_autotune)
     if args.served:
         plan = [(float(x.split(":")[0]), int(x.split(":")[1])) for x in args.served.split(",")]
         line["served"] = served_block(ctx, gbs, gi, plan, args.served_attempts, args.served_width, args.served_one)

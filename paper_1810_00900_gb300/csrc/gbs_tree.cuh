@@ -327,7 +327,10 @@ struct Dfs {
       // costs two fused multiply-adds.  A one-mode node needs only det(P).
       const double p00 = c[tri(OFF, OFF)], p11 = c[tri(OFF + 1, OFF + 1)], p10 = c[tri(OFF + 1, OFF)];
       if constexpr (Q == 1) {
-        const double g = rsqrt_(fma(p00, p11, -p10 * p10));
+        // det > 0 alone admits a negative definite block: p00 > 0 is tested on its bits
+        // (integer pipe), and a failed test turns g into NaN like any other bad pivot
+        const double g0 = rsqrt_(fma(p00, p11, -p10 * p10));
+        const double g = __double_as_longlong(p00) > 0 ? g0 : __longlong_as_double(0x7ff8000000000000ll);
         if (NEG) { acc.in = fma(s, g, acc.in); acc.ep += s; } else { acc.ip = fma(s, g, acc.ip); acc.en += s; }
       } else {
         constexpr int DN = 2 * Q - 2;
