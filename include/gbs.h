@@ -247,6 +247,24 @@ gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* st, int n_samples, uint64_t
                       const int* forced_clicks, int prec, uint8_t* patterns, double* p0_out,
                       gbs_sample_stats* stats);
 
+/* The paper's forced-outcome benchmark with the click positions drawn from the
+ * seed (Sec. III B: the walltime runs force the clicks on chosen modes and time
+ * the chain, which still evaluates p0 at every step): sample i is forced to
+ * click on the n_clicks modes gbs_draw_click_positions gives for it, then run as
+ * gbs_sample with those positions (one attempt).  Arguments and errors as for
+ * gbs_sample (1 <= n_clicks <= 31). */
+gbs_status gbs_sample_forced_random(gbs_ctx* ctx, const gbs_state* st, int n_samples, uint64_t seed, int n_clicks,
+                                    int prec, uint8_t* patterns, double* p0_out, gbs_sample_stats* stats);
+
+/* The click positions gbs_sample_forced_random uses (host only, no GPU): for
+ * sample i, n_clicks distinct modes of M from a partial Fisher-Yates shuffle
+ * driven by outputs i*n_clicks + 1 .. (i+1)*n_clicks of the SplitMix64 stream
+ * (Steele, Lea, Flood 2014) with state mix64(seed * 0x9E3779B97F4A7C15 +
+ * 6 * 0xD1B54A32D192ED03): draw c picks index c + floor(u (M - c)), u the top 53
+ * bits of the output times 2^-53; each sample's modes are returned sorted.
+ * out: caller-owned n_samples x n_clicks ints.  Errors: GBS_EINVAL. */
+gbs_status gbs_draw_click_positions(int M, int n_clicks, uint64_t seed, int n_samples, int* out);
+
 /* ---------------------------------------------------------- request loop -- */
 
 typedef enum { GBS_REQ_PROB = 0, GBS_REQ_SAMPLE = 1 } gbs_req_kind;

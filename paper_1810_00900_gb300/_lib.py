@@ -99,6 +99,10 @@ def load() -> ctypes.CDLL:
         "gbs_ctx_enable_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
         "gbs_ctx_kernel_time": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
         "gbs_ctx_host_gaps": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+        "gbs_draw_click_positions": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, _ip]),
+        "gbs_sample_forced_random": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.POINTER(ctypes.c_uint8), _dp,
+                                                    ctypes.POINTER(gbs_sample_stats)]),
         "gbs_measure_fp64_peak": (ctypes.c_int, [_vp, _dp]),
         "gbs_build_state": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, ctypes.POINTER(_vp)]),
         "gbs_state_from_V": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(_vp)]),
@@ -362,6 +366,33 @@ def sample(ctx: Context, st: State, n_samples: int, seed: int, N_post: int = 0, 
     sd["trees"] = list(sd["trees"])
     sd["tree_seconds"] = list(sd["tree_seconds"])
     return pats, p0, sd, status
+
+
+def draw_click_positions(M: int, n_clicks: int, seed: int, n_samples: int) -> np.ndarray:
+    """The seed-drawn forced click positions (gbs_draw_click_positions; host only)."""
+    out = np.zeros((max(n_samples, 0), n_clicks), dtype=np.int32)
+    st = load().gbs_draw_click_positions(int(M), int(n_clicks), ctypes.c_uint64(seed & ((1 << 64) - 1)),
+                                         int(n_samples), _i(out) if out.size else None)
+    if st != OK:
+        raise GbsError(st, "gbs_draw_click_positions")
+    return out
+
+
+def sample_forced_random(ctx: Context, st: State, n_samples: int, seed: int, n_clicks: int, prec: str = "auto",
+                         want_p0: bool = False):
+    """Forced-outcome samples with seed-drawn click positions (gbs_sample_forced_random):
+    (patterns, p0 or None, stats dict)."""
+    M = st.M
+    pats = np.zeros((n_samples, M), dtype=np.uint8)
+    p0 = np.zeros((n_samples, M)) if want_p0 else None
+    stats = gbs_sample_stats()
+    ctx.check(ctx.L.gbs_sample_forced_random(ctx.h, st.h, n_samples, ctypes.c_uint64(seed & ((1 << 64) - 1)),
+                                             n_clicks, PREC[prec], pats.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                             _p(p0) if want_p0 else None, ctypes.byref(stats)))
+    sd = {f: getattr(stats, f) for f, _ in gbs_sample_stats._fields_}
+    sd["trees"] = list(sd["trees"])
+    sd["tree_seconds"] = list(sd["tree_seconds"])
+    return pats, p0, sd
 
 
 class Server:

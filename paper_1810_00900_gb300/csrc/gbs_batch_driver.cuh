@@ -1,7 +1,6 @@
 // Host side of the batched tree engine: plan (segments, regions), upload, launches.
 #pragma once
 #include <algorithm>
-#include <mutex>
 #include <cstring>
 #include <vector>
 
@@ -21,24 +20,6 @@ struct Blob {
   }
 };
 
-
-// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the current
-// device, calling the runtime only when the limit must grow (every evaluation
-// would otherwise pay for the call).  One cache per kernel instantiation (Tag).
-template <class Tag>
-gbs_status smem_limit(gbs_ctx* ctx, const void* kernel, size_t bytes, const char* what) {
-  static std::mutex mu;
-  static int set_for[64] = {};
-  const int dev = ctx->device;
-  std::lock_guard<std::mutex> g(mu);
-  if (dev >= 0 && dev < 64 && set_for[dev] >= (int)bytes && set_for[dev] > 0) return GBS_OK;
-  gbs_status st = check_cuda(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
-                             what);
-  if (!st && dev >= 0 && dev < 64) set_for[dev] = (int)bytes;
-  return st;
-}
-template <class E> struct TopTag {};
-template <class E, int Q, bool PAIR> struct SubTag {};
 
 // PAIR: the last two levels of every tree as cancellation-free groups (FP64
 // real basis; the tree's inc output then carries the whole Torontonian).
@@ -205,7 +186,10 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
   // ---------------- top
   // The opt-in limit is set whatever the size: the kernels' static shared
   // memory (reduction scratch) counts against the default 48 KB as well.
-  if ((st = smem_limit<TopTag<E>>(ctx, (const void*)batch_top_kernel<E>, smem_top, "top smem"))) return st;
+  if ((st = check_cuda(ctx, cudaFuncSetAttribute(batch_top_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem_top),
+                       "top smem")))
+    return st;
   batch_top_kernel<E><<<(unsigned)top_blocks, tune.top_threads, smem_top, s>>>(
       (const TopSeg*)(plan + o_top), ntrees, (const typename root_src<E>::type*)roots_dev, buf[0], buf[1], sb[0], sb[1],
       status_dev, capA_top, capB_top, mid_off, ncap);
@@ -240,8 +224,10 @@ gbs_status batch_run(gbs_ctx* ctx, int ntrees, const BatchTree* trees, const voi
   case QQ:                                                                                                             \
     if constexpr (QQ <= QMAX) {                                                                                        \
       if (sub_e > 0) {                                                                                                 \
-        if ((st = smem_limit<SubTag<E, QQ, PAIR>>(ctx, (const void*)batch_subtree_kernel<E, QQ, PAIR>, smem_sub,     \
-                                                  "subtree smem")))                                                    \
+        if ((st = check_cuda(ctx,                                                                                      \
+                             cudaFuncSetAttribute(batch_subtree_kernel<E, QQ, PAIR>,                                   \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sub),         \
+                             "subtree smem")))                                                                         \
           return st;                                                                                                   \
         batch_subtree_kernel<E, QQ, PAIR><<<(unsigned)grid, nthr, smem_sub, s>>>(                                      \
             (const SubSeg*)(plan + o_leaf[qv]), ns, nb, buf[0], buf[1], sb[0], sb[1], capA, capB, pp,                  \

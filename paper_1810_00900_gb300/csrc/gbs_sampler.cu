@@ -615,3 +615,43 @@ extern "C" gbs_status gbs_sample(gbs_ctx* ctx, const gbs_state* cst, int n_sampl
   if (!all) return set_error(ctx, GBS_EREJECT, "postselection attempts exhausted for some samples");
   return GBS_OK;
 }
+
+// ------------------------------------------------- seed-drawn click positions --
+namespace {
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+}  // namespace
+
+extern "C" gbs_status gbs_draw_click_positions(int M, int n_clicks, uint64_t seed, int n_samples, int* out) {
+  if (M < 1 || n_clicks < 0 || n_clicks > M || n_clicks > kMaxClicks || n_samples < 0 || (!out && n_samples))
+    return GBS_EINVAL;
+  // stream "clicks" (identifier 6) of the workload seed, then output n = start + 1, start + 2, ...
+  const uint64_t s = mix64(seed * kGamma + 6ull * 0xD1B54A32D192ED03ull);
+  std::vector<int> perm(M);
+  for (int i = 0; i < n_samples; ++i) {
+    for (int j = 0; j < M; ++j) perm[j] = j;
+    const uint64_t start = (uint64_t)i * (uint64_t)n_clicks;
+    for (int c = 0; c < n_clicks; ++c) {
+      const double u = (double)(mix64(s + (start + (uint64_t)c + 1ull) * kGamma) >> 11) * 0x1p-53;
+      const int j = c + (int)(u * (double)(M - c));
+      std::swap(perm[c], perm[j]);
+    }
+    std::sort(perm.begin(), perm.begin() + n_clicks);
+    for (int c = 0; c < n_clicks; ++c) out[(long long)i * n_clicks + c] = perm[c];
+  }
+  return GBS_OK;
+}
+
+extern "C" gbs_status gbs_sample_forced_random(gbs_ctx* ctx, const gbs_state* st, int n_samples, uint64_t seed,
+                                               int n_clicks, int prec, uint8_t* patterns, double* p0_out,
+                                               gbs_sample_stats* stats) {
+  if (!ctx || !st || n_samples < 1 || n_clicks < 1) return GBS_EINVAL;
+  std::vector<int> pos((size_t)n_samples * n_clicks);
+  gbs_status e = gbs_draw_click_positions(st->M, n_clicks, seed, n_samples, pos.data());
+  if (e) return e;
+  return gbs_sample(ctx, st, n_samples, seed, n_clicks, 1, pos.data(), prec, patterns, p0_out, stats);
+}

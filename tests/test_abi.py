@@ -1,6 +1,8 @@
 """The C ABI library builds, loads without a GPU and exports every declared symbol."""
 import ctypes
 
+import numpy as np
+
 import pytest
 
 from paper_1810_00900_gb300 import _lib, build
@@ -36,3 +38,17 @@ def test_no_gpu_context_fails_cleanly(libpath):
         pytest.skip("a GPU is present")
     with pytest.raises(_lib.GbsError):
         _lib.Context(0)
+
+
+def test_seed_drawn_click_positions_follow_the_published_generator(libpath):
+    # gbs_draw_click_positions runs on the host: it must give the positions the seeded input
+    # generator's definition gives (SplitMix64 stream "clicks", partial Fisher-Yates, sorted)
+    import gbs_inputs as gi
+    import paper_1810_00900_gb300 as gbs
+    for M, n, seed, count in ((800, 20, 2, 5), (7, 3, 5, 4), (60, 8, 2, 1), (12, 12, 9, 2)):
+        got = gbs.draw_click_positions(M, n, seed, count)
+        want = np.array([gi.random_modes(M, n, seed, stream="clicks", start=i * n) for i in range(count)])
+        assert np.array_equal(got, want), (M, n, seed)
+    # the benchmark's forced trajectories are exactly these draws
+    _, clicks = gi.chain_sampling_workload(800, 20, 4, seed=2)
+    assert np.array_equal(gbs.draw_click_positions(800, 20, 2, 4), np.array(clicks))

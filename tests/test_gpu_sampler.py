@@ -108,3 +108,18 @@ def test_forced_trajectory_fixed_point_equals_triple_double(ctx):
     assert np.max(np.abs(p_fn - p_td)) < 1e-15
     assert s_fx["trees"][3] > 0 and s_fx["trees"][2] == 0 and s_td["trees"][2] > 0 and s_fw["trees"][4] > 0
     assert s_fn["trees"][5] > 0
+
+
+def test_forced_random_positions_equal_explicit_positions(ctx):
+    # gbs_sample_forced_random draws the click positions from the seed and runs the forced chain:
+    # the same as gbs_sample given those positions, and p0 at every step as the oracle's chain
+    M = 40
+    st, Sig = make(ctx, M, 8, r=(0.4, 0.9), eta=0.9)
+    pos = gbs.draw_click_positions(M, 6, 17, 3)
+    pats, p0, stats = gbs.sample_forced_random(ctx, st, 3, seed=17, n_clicks=6, want_p0=True)
+    pats2, p02, _, status = gbs.sample(ctx, st, 3, seed=17, N_post=6, forced_clicks=pos, want_p0=True)
+    assert status == 0 and np.array_equal(pats, pats2) and np.array_equal(p0, p02)
+    for i in range(3):
+        assert np.nonzero(pats[i])[0].tolist() == pos[i].tolist()
+    ref = oracle.sample_chain(Sig, 17, sample=0, forced_clicks=pos[0])
+    assert np.allclose(p0[0], np.array(ref["p0"]), rtol=0, atol=1e-10)
