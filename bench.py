@@ -54,22 +54,22 @@ def survey_flops(q: int, complex_basis: bool = False) -> float:
 
 def executed_flops(q: int, Q: int, complex_basis: bool = False) -> float:
     """FP64 flops the kernels execute below a node with q undecided modes when the
-    last Q levels run in registers (FMA = 2, any other operation = 1; the inverse
-    square root as its three FMAs).  Levels above the register subtree (shared
-    memory) factor the pivot by its adjugate: det, rsqrt, 1/det, the scaled
-    inverse, L = u P^-1 (3 flops per entry of 2t rows) and the update (two FMAs per
-    lower-triangle entry).  The real-basis register levels factor it by Cholesky
-    (two rsqrts, rows w = u R^-T at 4 flops per row); one-mode nodes form det and
-    its rsqrt and add their two leaf terms (one FMA, one add).  Complex entries
-    count 4x the real flops of the same formulas."""
+    last Q levels run in registers (FMA = 2, any other FP64 operation = 1; the
+    inverse square roots run on the integer pipes and count 0).  Levels above the
+    register subtree (shared memory) factor the pivot by its adjugate: det (3),
+    1/det (1), the scaled inverse (3), s g (1), L = u P^-1 (3 flops per entry of 2t
+    rows) and the update (two FMAs per lower-triangle entry).  The real-basis
+    register levels factor it by Cholesky (w, d1, g, the row coefficient, s g: 6;
+    rows w = u R^-T at 4 flops per row); one-mode nodes form det (3) and add their
+    two leaf terms (one FMA, one add: 3).  Complex entries count 4x the real flops."""
     def node(k, reg):
         t = k - 1
         if k == 1:
-            return 12.0
+            return 6.0
         sym2t = t * (2 * t + 1)
         if reg and not complex_basis:
-            return 18.0 + 8.0 * t + 4.0 * sym2t
-        return 14.0 + 12.0 * t + 4.0 * sym2t
+            return 6.0 + 8.0 * t + 4.0 * sym2t
+        return 8.0 + 12.0 * t + 4.0 * sym2t
     total = 0.0
     for k in range(1, q + 1):
         total += 2.0 ** (q - k) * node(k, k <= Q)
@@ -189,7 +189,10 @@ def captured_traffic(args, tuning):
 
 # (prec, basis, N, sub_e, q_drop) -> bytes per launch of the subtree kernel, dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of the current kernel code
-CAPTURED_TRAFFIC = {}
+CAPTURED_TRAFFIC = {
+    # 2^15 depth-15 roots of 171 entries (44.8 MB of input) into one-warp CTAs of two roots each
+    ("fp64", "real", 24, 4, 0): 45235456 + 4096000,
+}
 
 
 def whole_job_rate(ws: int, units_per_rank: float, seconds_max: float) -> float:
@@ -813,7 +816,8 @@ def main():
             "flop_model": "8 t^2 flops per rank-2 update of 2t rows (real basis) + rsqrt and add per subset term",
             "flops_per_launch": leaf_flops, "leaf_ms_avg": leaf_avg_s * 1e3,
             "executed": {"flops_per_launch": leaf_exec, "achieved": achieved_exec, "frac": achieved_exec / peak,
-                         "model": "every FP64 operation the kernel executes (FMA = 2, other = 1, rsqrt = 3 FMAs)"},
+                         "model": "every FP64 operation the kernel executes (FMA = 2, other = 1; the inverse "
+                                  "square roots run on the integer pipes)"},
             "step_flops": total_flops,
             "step_tflops": total_flops * args.steps / (dev_ms * 1e-3) / 1e12,
             "other_accountings": other_accountings(args.N, dev_ms * 1e-3 / args.steps),

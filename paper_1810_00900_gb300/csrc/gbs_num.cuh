@@ -152,66 +152,26 @@ __device__ __forceinline__ td rsqrt_(td a) {
 }
 
 // ------------------------------------------ FP64 inverse square root -----
-// 1/sqrt(x) for double x in three FP64-pipe instructions.  On this GPU the
+// 1/sqrt(x) for double x with no FP64 instruction at all.  On this GPU the
 // FP64 pipe issues 2 fused multiply-adds per clock per SM against 128 FP32
-// and ~64 32-bit integer operations, so the seed is formed off that pipe:
-//   1. x = m 2^ex with m in [1, 2) is written as x' 2^(2k), x' = m 2^(ex mod 2)
-//      in [1, 4); the leading 24 bits of x' become a float xf (integer ops);
-//   2. yf = rsqrtf(xf) (the FP32 special-function unit, relative error
-//      below 2^-21 with the truncation of x' included);
-//   3. y0 = yf 2^-k, y0/2, ~3 y0/8 and yf^2 (exact: 48 bits) are assembled as
-//      doubles from the float's bits (integer ops);
-// then one Newton-Raphson step of the third order (the Taylor series of
-// (1 - e)^(-1/2) to e^2):
-//   e = 1 - x' yf^2                      (one fused multiply-add, yf^2 exact)
-//   y = y0 + (y0/2) e + (3 y0/8) e^2     (two fused multiply-adds)
-// |e| < 2^-20, so the dropped 5 e^3 / 16 term is below 2^-61; the result is
-// within about 1 ulp.  x that is not a positive normal double (zero, negative,
-// subnormal, inf, NaN) gives NaN.
-__device__ __forceinline__ double rsqrt_f64(double x) {
-  const int hi = __double2hiint(x);
-  const unsigned lo = (unsigned)__double2loint(x);
-  const int eb = hi >> 20;  // biased exponent; negative for x < 0
-  const bool ok = (unsigned)(eb - 1) < 0x7feu;
-  const int ex = eb - 1023;
-  const int r = ex & 1;
-  const int k = ex >> 1;  // floor(ex / 2)
-  const double xr = __hiloint2double((hi & 0x000fffff) | ((1023 + r) << 20), (int)lo);
-  const float xf = __int_as_float(((127 + r) << 23) | ((hi & 0x000fffff) << 3) | (int)(lo >> 29));
-  const float yf = rsqrtf(xf);
-  const unsigned yb = __float_as_uint(yf);
-  const unsigned my = (yb & 0x7fffffu) | 0x800000u;  // 24-bit significand of yf
-  const int ey = (int)(yb >> 23) - 127;
-  // yf^2 = my^2 2^(2 ey - 46), my^2 in [2^46, 2^48)
-  const unsigned long long p = (unsigned long long)my * my;
-  const int l47 = (int)(p >> 47);
-  const unsigned long long f2 = p << (6 - l47);  // leading bit at 52
-  const double yf2 = __hiloint2double((int)(((unsigned)(2 * ey + l47 + 1023) << 20) | (unsigned)((f2 >> 32) & 0xfffffu)),
-                                      (int)(unsigned)f2);
-  const double e = fma(-xr, yf2, 1.0);
-  const int ez = ey - k + 1023;
-  const int fh = (int)((my & 0x7fffffu) >> 3), fl = (int)((my & 7u) << 29);
-  const double y0 = __hiloint2double((ez << 20) | fh, fl);
-  const double c12 = __hiloint2double(((ez - 1) << 20) | fh, fl);
-  const unsigned cb = __float_as_uint(0.375f * yf);  // only ~12 of its bits matter
-  const double c38 = __hiloint2double((int)((((cb >> 23) - 127 - k + 1023) << 20) | ((cb & 0x7fffffu) >> 3)),
-                                      (int)((cb & 7u) << 29));
-  const double y = fma(fma(c38, e, c12), e, y0);
-  return ok ? y : __longlong_as_double(0x7ff8000000000000ll);
-}
-
-// 1/sqrt(x) for double x with no FP64 instruction at all: the FP32 seed of
-// rsqrt_f64, then the same third-order Newton-Raphson step in integer
-// arithmetic.  With x = M 2^(ex - 52) (M the 53-bit significand, ex = 2k + r)
-// and yf = my 2^(ey - 23):
-//   x' yf^2 = M my^2 2^-sh, sh = 98 - r - 2 ey, so D = 2^sh - M my^2 (a
-//   128-bit difference, exact) gives E = e 2^64 = floor(D 2^(64 - sh)),
-//   |E| < 2^45 (|e| < 2^-19);
-//   F = (e/2 + 3 e^2/8) 2^64 = E/2 + 3 (E^2 / 2^64) / 8;
-//   Y = my (2^64 + F), an 89-bit integer, rounded to 53 bits (half up) is the
-//   significand of y = Y 2^(ey - 87 - k).
+// operations and ~64 32-bit integer operations, so the whole routine runs off
+// that pipe:
+//   1. x = M 2^(ex - 52) (M the 53-bit significand) is written as x' 2^(2k),
+//      x' = M 2^(r - 52) in [1, 4), r = ex mod 2; the leading 24 bits of x'
+//      become a float xf (integer ops);
+//   2. yf = rsqrtf(xf) = my 2^(ey - 23) (the FP32 special-function unit,
+//      relative error below 2^-21 with the truncation of x' included);
+//   3. one Newton-Raphson step of the third order (the Taylor series of
+//      (1 - e)^(-1/2) to e^2), y = y0 (1 + e/2 + 3 e^2/8), y0 = yf 2^-k, in
+//      integer arithmetic:
+//        x' yf^2 = M my^2 2^-sh, sh = 98 - r - 2 ey, so D = 2^sh - M my^2 (a
+//        128-bit difference, exact) gives E = e 2^64 = floor(D 2^(64 - sh)),
+//        |E| < 2^45 (|e| < 2^-19);
+//        F = (e/2 + 3 e^2/8) 2^64 = E/2 + 3 (E^2 / 2^64) / 8;
+//        Y = my (2^64 + F), an 89-bit integer, rounded to 53 bits (half up) is
+//        the significand of y = Y 2^(ey - 87 - k).
 // Truncations of E and F cost at most a few units of 2^-64 and the dropped
-// 5 e^3/16 below 2^-55, so the result is within 0.51 ulp.  Non-positive,
+// 5 e^3/16 stays below 2^-55, so the result is within 0.51 ulp.  Non-positive,
 // subnormal, inf and NaN inputs give NaN.
 __device__ __forceinline__ double rsqrt_i64(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -258,13 +218,7 @@ GBS_HD float fms(float x, float a, float b) { return fmaf(-a, b, x); }
 GBS_HD float fpa(float x, float a, float b) { return fmaf(a, b, x); }
 GBS_HD double to_double(double a) { return a; }
 GBS_HD double to_double(float a) { return (double)a; }
-#if defined(GBS_EXPERIMENT_CUDA_RSQRT)
-__device__ __forceinline__ double rsqrt_(double a) { return rsqrt(a); }
-#elif defined(GBS_EXPERIMENT_FMA_RSQRT)
-__device__ __forceinline__ double rsqrt_(double a) { return rsqrt_f64(a); }
-#else
 __device__ __forceinline__ double rsqrt_(double a) { return rsqrt_i64(a); }
-#endif
 __device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
 
 template <class T> GBS_HD T from_double(double a);

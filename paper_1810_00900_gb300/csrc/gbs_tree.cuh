@@ -300,75 +300,6 @@ __device__ __forceinline__ void pair_single(const double (&c)[sym(D)], double s,
 }
 
 // ----------------------------------------------- register depth-first ----
-#ifdef GBS_EXPERIMENT_ADJUGATE
-constexpr bool kExperimentAdjugate = true;
-#else
-constexpr bool kExperimentAdjugate = false;
-#endif
-// FP64 real basis with the pivot factors of both children formed as early as
-// their inputs exist: the excluded child's (the parent's next 2 x 2 block) before
-// the included child's rank-2 update, the included child's right after the
-// update's first two rows.  Their integer inverse-square-root chains can then
-// run beside the FP64 work of the update instead of in front of it.
-struct CholPiv {
-  double r0, w, r1;  // r0 = p00^(-1/2), w = p10 r0, r1 = (p11 - w^2)^(-1/2)
-};
-__device__ __forceinline__ CholPiv chol_piv(double p00, double p11, double p10) {
-  CholPiv v;
-  v.r0 = rsqrt_(p00);
-  v.w = p10 * v.r0;
-  v.r1 = rsqrt_(fma(-v.w, v.w, p11));
-  return v;
-}
-__device__ __forceinline__ double leaf_g(double p00, double p11, double p10) {
-  const double g0 = rsqrt_(fma(p00, p11, -p10 * p10));
-  return __double_as_longlong(p00) > 0 ? g0 : __longlong_as_double(0x7ff8000000000000ll);
-}
-template <int Q> struct PivOf { typedef CholPiv type; };
-template <> struct PivOf<1> { typedef double type; };
-template <int Q, int D, int OFF>
-__device__ __forceinline__ typename PivOf<Q>::type piv_at(const double (&c)[sym(D)]) {
-  if constexpr (Q == 1)
-    return leaf_g(c[tri(OFF, OFF)], c[tri(OFF + 1, OFF + 1)], c[tri(OFF + 1, OFF)]);
-  else
-    return chol_piv(c[tri(OFF, OFF)], c[tri(OFF + 1, OFF + 1)], c[tri(OFF + 1, OFF)]);
-}
-template <int Q, int D, int OFF, bool NEG>
-struct DfsEarly {
-  static __device__ __forceinline__ void run(const double (&c)[sym(D)], double s, Sums<double>& acc,
-                                             const typename PivOf<Q>::type& pv) {
-    if constexpr (Q == 1) {
-      if (NEG) { acc.in = fma(s, pv, acc.in); acc.ep += s; } else { acc.ip = fma(s, pv, acc.ip); acc.en += s; }
-    } else {
-      constexpr int DN = 2 * Q - 2;
-      const double g = pv.r0 * pv.r1;
-      const double kap = -pv.w * g;
-      const typename PivOf<Q - 1>::type ex = piv_at<Q - 1, D, OFF + 2>(c);
-      double w0[DN], w1[DN];
-#pragma unroll
-      for (int a = 0; a < DN; ++a) {
-        const double u0 = c[tri(OFF + 2 + a, OFF)], u1 = c[tri(OFF + 2 + a, OFF + 1)];
-        w0[a] = u0 * pv.r0;
-        w1[a] = fma(u0, kap, u1 * pv.r1);
-      }
-      double cn[sym(DN)];
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b <= a; ++b)
-          cn[tri(a, b)] = fma(-w1[a], w1[b], fma(-w0[a], w0[b], c[tri(OFF + 2 + a, OFF + 2 + b)]));
-      const typename PivOf<Q - 1>::type in = piv_at<Q - 1, DN, 0>(cn);
-#pragma unroll
-      for (int a = 2; a < DN; ++a)
-#pragma unroll
-        for (int b = 0; b <= a; ++b)
-          cn[tri(a, b)] = fma(-w1[a], w1[b], fma(-w0[a], w0[b], c[tri(OFF + 2 + a, OFF + 2 + b)]));
-      DfsEarly<Q - 1, DN, 0, NEG>::run(cn, s * g, acc, in);
-      DfsEarly<Q - 1, D, OFF + 2, !NEG>::run(c, s, acc, ex);
-    }
-  }
-};
-
 // Node with Q undecided modes whose matrix is the view c[tri(OFF + i, OFF + j)]
 // of an array of dimension D; NEG = odd number of exclusions above it.  PAIR:
 // the last two levels as cancellation-free groups (above; E = double only).
@@ -381,7 +312,7 @@ struct Dfs {
     if constexpr (PAIR && Q <= 2) {
       static_assert(std::is_same<E, double>::value, "the paired last levels are FP64 real-basis only");
       if constexpr (Q == 2) pair_group<D, OFF, NEG>(c, s, acc); else pair_single<D, OFF, NEG>(c, s, acc);
-    } else if constexpr (std::is_same<E, double>::value && !kExperimentAdjugate) {
+    } else if constexpr (std::is_same<E, double>::value) {
       // FP64 real basis, the pivot block factored as P = R R^T (Cholesky):
       //   r0 = p00^(-1/2), w = p10 r0, d1 = p11 - w^2, r1 = d1^(-1/2),
       //   det(P)^(-1/2) = r0 r1,
@@ -389,10 +320,6 @@ struct Dfs {
       //   w0 = u0 r0,  w1 = (u1 - w0 w) r1 = u1 r1 + u0 (-w r0 r1),
       // three FP64 instructions per row where u P^-1 takes four; an entry still
       // costs two fused multiply-adds.  A one-mode node needs only det(P).
-#ifdef GBS_EXPERIMENT_EARLY_PIVOT
-      DfsEarly<Q, D, OFF, NEG>::run(c, s, acc, piv_at<Q, D, OFF>(c));
-      if (false) {
-#endif
       const double p00 = c[tri(OFF, OFF)], p11 = c[tri(OFF + 1, OFF + 1)], p10 = c[tri(OFF + 1, OFF)];
       if constexpr (Q == 1) {
         // det > 0 alone admits a negative definite block: p00 > 0 is tested on its bits
@@ -423,9 +350,6 @@ struct Dfs {
         Dfs<E, Q - 1, DN, 0, NEG, PAIR>::run(cn, s * g, acc, bad);
         Dfs<E, Q - 1, D, OFF + 2, !NEG, PAIR>::run(c, s, acc, bad);
       }
-#ifdef GBS_EXPERIMENT_EARLY_PIVOT
-      }
-#endif
     } else {
     const T p00 = re_of(c[tri(OFF, OFF)]);
     const T p11 = re_of(c[tri(OFF + 1, OFF + 1)]);
