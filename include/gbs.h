@@ -141,6 +141,16 @@ gbs_status gbs_ctx_host_gaps(gbs_ctx* ctx, double* seconds, long long* waits);
  * has no GPU counterpart; it reports CPU walltimes only (Sec. III, Table II). */
 gbs_status gbs_measure_fp64_peak(gbs_ctx* ctx, double* gflops);
 
+/* Fixed-point product throughput of this GPU, measured now: a full grid (16
+ * warps per SM) of four independent chains of dependent products per thread,
+ * in the FX entry type (six 32-bit limbs, 160 fraction bits: 26 partial
+ * products of 32 x 32 bits each), no memory traffic, best of three timed
+ * launches on the context stream.  *products_per_s receives products per
+ * second.  The denominator of the integer-pipe roofline of the fixed-point
+ * trees, whose work is counted in these products (the paper's quadruple
+ * precision of Sec. III A, carried out in integer arithmetic here). */
+gbs_status gbs_measure_fx_peak(gbs_ctx* ctx, double* products_per_s);
+
 /* -------------------------------------------------------------- states -- */
 
 /* Build the state of M single-mode squeezers r[0..M-1] followed by the M x M

@@ -104,6 +104,7 @@ def load() -> ctypes.CDLL:
                                                     ctypes.POINTER(ctypes.c_uint8), _dp,
                                                     ctypes.POINTER(gbs_sample_stats)]),
         "gbs_measure_fp64_peak": (ctypes.c_int, [_vp, _dp]),
+        "gbs_measure_fx_peak": (ctypes.c_int, [_vp, _dp]),
         "gbs_build_state": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, ctypes.POINTER(_vp)]),
         "gbs_state_from_V": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(_vp)]),
         "gbs_state_free": (None, [_vp]),
@@ -200,6 +201,12 @@ class Context:
         """Measured FP64 rate of the device in GFLOP/s."""
         g = ctypes.c_double()
         self.check(self.L.gbs_measure_fp64_peak(self.h, ctypes.byref(g)))
+        return g.value
+
+    def measure_fx_peak(self) -> float:
+        """Measured rate of 192-bit fixed-point products (the FX entry type) in products/s."""
+        g = ctypes.c_double()
+        self.check(self.L.gbs_measure_fx_peak(self.h, ctypes.byref(g)))
         return g.value
 
     def autotune(self, prec: str = "fp64", basis: str = "real", n: int = 22, n_trees: int = 1):

@@ -41,3 +41,23 @@ def test_gpu_arm_line():
     assert d["gpu_launches"] > 0 and d["value"] > 0 and d["e2e"]["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_fx_product_model():
+    # the closed sum over depths equals the recursion over the tree's nodes, and the one- and
+    # two-mode trees come out at their hand counts
+    sys.path.insert(0, ROOT)
+    import bench
+    R, SG = 89.0 / 26.0, 39.0 / 26.0
+
+    def walk(m):  # products below (and including) one node with m undecided modes
+        if m == 1:
+            return 2.0 + R + SG
+        t = m - 1
+        here = 2.0 + R + 1.0 + 3.0 + SG + 8.0 * t + 2.0 * t * (2 * t + 1)
+        return here + 2.0 * walk(m - 1)
+
+    assert bench.fx_products(1) == 2.0 + R + SG
+    assert bench.fx_products(2) == (2.0 + R + 1.0 + 3.0 + SG + 8.0 + 6.0) + 2.0 * (2.0 + R + SG)
+    for n in range(1, 16):
+        assert abs(bench.fx_products(n) - walk(n)) <= 1e-9 * walk(n)

@@ -63,3 +63,15 @@ def test_autotune_picks_a_candidate(ctx):
     chosen = [r for r in rep if all(r[k] == t[k] for k in keys)]
     # the report rounds to 0.1 us, so several candidates can tie with the one kept
     assert len(chosen) == 1 and chosen[0]["ms"] == best
+
+
+def test_peak_probes(ctx):
+    # the roofline denominators: FP64 at most 2 FMAs per clock per SM, fixed-point products
+    # between a tenth of one and four per clock per SM (26 partial products of 32 x 32 bits each)
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    sms, ghz = props.multi_processor_count, 2.2
+    g = ctx.measure_fp64_peak()
+    assert 0 < g <= 2 * 2 * sms * ghz * 1.01
+    p = ctx.measure_fx_peak()
+    assert 0.1 * sms * 1.0e9 < p < 4 * sms * ghz * 1e9
