@@ -93,42 +93,61 @@ def fx_products(n: int) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+    """nvidia-smi samples (every 20 ms) around the timed region; the samples read between
+    begin() and end() (plus one sampling period) are the ones reported."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, device: int):
         self.device = device
         self.proc = None
         self.lines = []
+        self.t_begin = self.t_end = None
 
     def start(self):
+        """Start sampling and wait (up to 3 s) for the first sample, so that the timed
+        region that follows is covered from its start."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 3.0:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def begin(self):
+        self.t_begin = time.perf_counter()
+
+    def end(self):
+        self.t_end = time.perf_counter()
 
     def stop(self):
         if not self.proc:
             return None
+        if self.t_end is None:
+            self.end()
+        time.sleep(2 * self.PERIOD_MS / 1e3)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        t_b = self.t_begin if self.t_begin is not None else -1e300
+        inside = [ln for t, ln in self.lines if t_b <= t <= self.t_end + self.PERIOD_MS / 1e3]
         sm, smax, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in inside:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -143,7 +162,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "period_ms": self.PERIOD_MS}
 
 
 def dist_setup():
@@ -200,14 +219,17 @@ def captured_traffic(args, tuning):
     """DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of the same
     kernel code and launch shape (FP64 real basis, N = 24, the shared-memory levels and register
     depth given here); None for any other shape, or once the kernel changed since the capture."""
-    return CAPTURED_TRAFFIC.get((args.prec, args.basis, args.N, tuning["sub_e"], tuning["q_drop"]))
+    return CAPTURED_TRAFFIC.get((args.prec, args.basis, args.N, tuning["sub_e"], tuning["q_drop"],
+                                 tuning["grid_per_sm"]))
 
 
-# (prec, basis, N, sub_e, q_drop) -> bytes per launch of the subtree kernel, dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture of the current kernel code
+# (prec, basis, N, sub_e, q_drop, grid_per_sm) -> bytes per launch of the subtree kernel,
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the current kernel code
 CAPTURED_TRAFFIC = {
-    # 2^15 depth-15 roots of 171 entries (44.8 MB of input) into one-warp CTAs of two roots each
-    ("fp64", "real", 24, 4, 0): 45235456 + 4096000,
+    # 2^15 depth-15 roots of 171 entries (44.8 MB of input) into one-warp CTAs of two roots each;
+    # one CTA per pair of roots (16,384 partials, which stay in L2) or 8 persistent CTAs per SM
+    ("fp64", "real", 24, 4, 0, 0): 45235456 + 39424,
+    ("fp64", "real", 24, 4, 0, 8): 45235456 + 4096000,
 }
 
 
@@ -687,7 +709,7 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp64p", "dd", "td", "fp32", "fxn", "fx", "fxw"])
@@ -768,6 +790,8 @@ def main():
     def step():
         return gbs.torontonian(ctx, st, modes, args.prec, args.basis)
 
+    clocks = ClockSampler(dev)
+    clocks.start()  # running before the warm-up, so it samples the whole timed region
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -775,10 +799,9 @@ def main():
     ctx.enable_timing(True)
     launches0 = ctx.launch_count
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(dev)
     barrier(ws)
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.begin()
     results = []
     for i in range(args.steps):
         with torch.cuda.stream(stream):
@@ -787,6 +810,7 @@ def main():
         results.append(step())
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     barrier(ws)
     clk = clocks.stop()
     launches = ctx.launch_count - launches0
