@@ -265,8 +265,14 @@ __global__ void __launch_bounds__(256, level_min_blocks<E>::value) batch_level_k
   const LevelSeg sg = segs[find_seg(segs, nseg, tid, &LevelSeg::thread_begin)];
   const long long local = tid - sg.thread_begin;
   const long long count = sg.count;
-  const long long node = local % count;
-  const int grp = (int)(local / count);
+  // Threads go over tiles of 32 consecutive nodes (the whole level when it has
+  // fewer): a warp holds one row group of 32 nodes, and the row groups of a tile
+  // follow one another, so the parent entries all groups read (pivot block,
+  // first two columns) are still in L1/L2 when the later groups read them.
+  const long long tile = (count & 31) ? count : 32;
+  const long long within = local % (tile * sg.groups);
+  const long long node = (local / (tile * sg.groups)) * tile + within % tile;
+  const int grp = (int)(within / tile);
   const int rows = 2 * sg.q - 2;
   const E* par = in + sg.in_base;
   const long long c2 = 2 * count;
