@@ -265,14 +265,24 @@ __global__ void __launch_bounds__(256, level_min_blocks<E>::value) batch_level_k
   const LevelSeg sg = segs[find_seg(segs, nseg, tid, &LevelSeg::thread_begin)];
   const long long local = tid - sg.thread_begin;
   const long long count = sg.count;
-  // Threads go over tiles of 32 consecutive nodes (the whole level when it has
-  // fewer): a warp holds one row group of 32 nodes, and the row groups of a tile
-  // follow one another, so the parent entries all groups read (pivot block,
-  // first two columns) are still in L1/L2 when the later groups read them.
-  const long long tile = (count & 31) ? count : 32;
-  const long long within = local % (tile * sg.groups);
-  const long long node = (local / (tile * sg.groups)) * tile + within % tile;
-  const int grp = (int)(within / tile);
+  // With up to 8 row groups, threads go over tiles of 32 consecutive nodes (the
+  // whole level when it has fewer): a warp holds one row group of 32 nodes and a
+  // 256-thread CTA whole tiles, so the parent entries all groups read (pivot
+  // block, first two columns) are still cached when the later groups read them,
+  // and a CTA's warps carry every row group (equal work).  With more groups a CTA
+  // would hold a few row groups of unequal cost; there one row group of
+  // consecutive nodes per CTA keeps its warps' work equal.
+  long long node;
+  int grp;
+  if (sg.groups <= 8) {
+    const long long tile = (count & 31) ? count : 32;
+    const long long within = local % (tile * sg.groups);
+    node = (local / (tile * sg.groups)) * tile + within % tile;
+    grp = (int)(within / tile);
+  } else {
+    node = local % count;
+    grp = (int)(local / count);
+  }
   const int rows = 2 * sg.q - 2;
   const E* par = in + sg.in_base;
   const long long c2 = 2 * count;
