@@ -300,10 +300,38 @@ __global__ void __launch_bounds__(256, level_min_blocks<E>::value) batch_level_k
   const T inv = g * g;
   const T q00 = p00 * inv, q11 = p11 * inv;
   const E m10 = neg_(scale_(p10, inv));
+  // 160- and 192-bit entries (level_park): the scaled pivot inverse and g wait
+  // in this thread's shared-memory slot while the rows are formed (read back
+  // once per row), which frees the registers the row loop would otherwise spill.
+  constexpr int LW = node_words<E>::value;
+  constexpr bool PARK = level_park<E>::value && LW > 0;
+  __shared__ uint32_t park[PARK ? 4 * LW : 1][PARK ? 256 : 1];
+  if constexpr (PARK) {
+#pragma unroll
+    for (int k = 0; k < LW; ++k) {
+      park[k][threadIdx.x] = q00.w[k];
+      park[LW + k][threadIdx.x] = q11.w[k];
+      park[2 * LW + k][threadIdx.x] = m10.w[k];
+      park[3 * LW + k][threadIdx.x] = g.w[k];
+    }
+  }
+  auto unpark = [&](int slot, const auto& keep) {
+    typedef typename std::decay<decltype(keep)>::type V;
+    if constexpr (PARK) {
+      V r;
+      const volatile uint32_t* src = &park[slot * LW][threadIdx.x];
+#pragma unroll
+      for (int k = 0; k < LW; ++k) r.w[k] = src[k * 256];
+      return r;
+    } else {
+      return keep;
+    }
+  };
   for (int a = grp; a < rows; a += sg.groups) {
     const E u0 = PAR(a + 2, 0), u1 = PAR(a + 2, 1);
-    const E L0 = lin2(u0, q11, u1, m10);
-    const E L1 = lin2(u1, q00, u0, conj_(m10));
+    const E m10r = unpark(2, m10);
+    const E L0 = lin2(u0, unpark(1, q11), u1, m10r);
+    const E L1 = lin2(u1, unpark(0, q00), u0, conj_(m10r));
     for (int b = 0; b < a; ++b) {
       const E x = PAR(a + 2, b + 2);
       E v = fms_conj(x, L0, PAR(b + 2, 0));
@@ -320,7 +348,7 @@ __global__ void __launch_bounds__(256, level_min_blocks<E>::value) batch_level_k
   if (grp == 0) {
     const typename scale_of<E>::type s = sin[sg.s_in + node];
     sout[sg.s_out + 2 * node] = s;
-    sout[sg.s_out + 2 * node + 1] = s * g;
+    sout[sg.s_out + 2 * node + 1] = s * unpark(3, g);
   }
 #undef PAR
 }

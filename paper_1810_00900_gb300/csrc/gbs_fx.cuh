@@ -240,9 +240,12 @@ template <int L, int F> GBS_HD bool is_pos(const fxn<L, F>& d) { return fx_det_i
 // Fixed-point trees run only on matrices the host has bounded (positive definite).
 template <int L, int F> GBS_HD bool lead_pos(const fxn<L, F>&) { return true; }
 template <> constexpr int bad_status<fxn4>() { return kStatusRange; }
-template <> struct level_min_blocks<fxn4> { static const int value = 3; };
+template <> struct level_min_blocks<fxn4> { static const int value = 4; };
+template <> struct level_park<fxn4> { static const bool value = true; };
 template <> constexpr int bad_status<fx>() { return kStatusRange; }
-template <> struct level_min_blocks<fx> { static const int value = 3; };
+template <> struct level_min_blocks<fx> { static const int value = 4; };
+template <> struct level_park<fx> { static const bool value = true; };
+template <> struct level_park<fxw> { static const bool value = true; };
 template <int L, int F> struct node_words<fxn<L, F>> { static const int value = L; };
 template <int L, int F> struct leaf_min_blocks<fxn<L, F>> { static const int value = 4; };
 template <> struct level_min_blocks<fxw> { static const int value = 3; };
