@@ -300,9 +300,9 @@ __global__ void __launch_bounds__(256, level_min_blocks<E>::value) batch_level_k
   const T inv = g * g;
   const T q00 = p00 * inv, q11 = p11 * inv;
   const E m10 = neg_(scale_(p10, inv));
-  // 160- and 192-bit entries (level_park): the scaled pivot inverse and g wait
-  // in this thread's shared-memory slot while the rows are formed (read back
-  // once per row), which frees the registers the row loop would otherwise spill.
+  // Fixed-point entries (level_park): the scaled pivot inverse and g wait in this
+  // thread's shared-memory slot while the rows are formed (read back once per
+  // row), which frees the registers the row loop would otherwise spill.
   constexpr int LW = node_words<E>::value;
   constexpr bool PARK = level_park<E>::value && LW > 0;
   __shared__ uint32_t park[PARK ? 4 * LW : 1][PARK ? 256 : 1];

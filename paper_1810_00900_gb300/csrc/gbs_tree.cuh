@@ -68,7 +68,8 @@ template <class E> struct scale_of { typedef typename real_of<E>::type type; };
 // too few warps otherwise.
 template <class E> struct level_min_blocks { static const int value = 1; };
 // Level kernel: keep the scaled pivot inverse and g in shared memory while the
-// rows are formed (multiword entries whose registers would otherwise spill).
+// rows are formed (the fixed-point entry types, whose registers would otherwise
+// spill).
 template <class E> struct level_park { static const bool value = false; };
 // The same for the register-subtree leaf kernel (128-thread CTAs).
 template <class E> struct leaf_min_blocks { static const int value = 1; };
