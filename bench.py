@@ -42,7 +42,7 @@ def sym(d):
     return d * (d + 1) // 2
 
 
-def survey_flops(q: int, complex_basis: bool = False) -> float:
+def leading_flops(q: int, complex_basis: bool = False) -> float:
     """Algorithmic flops of the subtree below a node with q undecided modes, the
     leading-order count of the method: the include child of a node with t + 1
     undecided modes does a rank-2 update of 2t rows, 4 t^2 real multiply-adds
@@ -406,10 +406,10 @@ def complex_basis_block(ctx, gbs, st, modes, steps, stream, peak):
     t = ctx.tuning("fp64", "complex")
     Q = max(1, min(4 - t["q_drop"], 24))
     q_root = min(24, Q + t["sub_e"])
-    leaf_flops = (2 ** (24 - q_root)) * survey_flops(q_root, True)
+    leaf_flops = (2 ** (24 - q_root)) * leading_flops(q_root, True)
     achieved = leaf_flops / (leaf_ms / max(leaf_n, 1) * 1e-3) / 1e12
     return {"metric": "Tor subset-terms/s (FP64, N=24, complex basis)", "value": 2.0 ** 24 / (ms * 1e-3),
-            "ms_per_evaluation": ms, "tuning": t, "survey_flops_per_term": survey_flops(24, True) / 2.0 ** 24,
+            "ms_per_evaluation": ms, "tuning": t, "leading_flops_per_term": leading_flops(24, True) / 2.0 ** 24,
             "dominant_kernel_tflops": achieved, "frac_of_fp64_peak": achieved / peak}
 
 
@@ -778,9 +778,9 @@ def main():
     Q = max(1, min(Q - tuning["q_drop"], args.N))
     q_root = min(args.N, Q + tuning["sub_e"])
     depth = args.N - q_root
-    leaf_flops = (2 ** depth) * survey_flops(q_root, complex_basis)
+    leaf_flops = (2 ** depth) * leading_flops(q_root, complex_basis)
     leaf_exec = (2 ** depth) * executed_flops(q_root, Q, complex_basis)
-    total_flops = survey_flops(args.N, complex_basis)
+    total_flops = leading_flops(args.N, complex_basis)
     kernel_name = ("batch_subtree_kernel (%d levels expanded in shared memory, then register depth-first %d levels)"
                    % (q_root - Q, Q)) if tuning["sub_e"] else "batch_leaf_kernel (register depth-first, %d levels)" % Q
 
