@@ -75,3 +75,26 @@ def test_peak_probes(ctx):
     assert 0 < g <= 2 * 2 * sms * ghz * 1.01
     p = ctx.measure_fx_peak()
     assert 0.1 * sms * 1.0e9 < p < 4 * sms * ghz * 1e9
+
+
+def test_small_levels_every_thread_mapping(ctx):
+    # Breadth-first levels of small trees, where a level has fewer than 32 nodes: with one row
+    # group per node, with a few (tiles of the whole level), and with more than 8 (one group of
+    # consecutive nodes per block).  Fixed point gives the same bits for every shape.
+    st = gi.uniform_squeezed_state(60, 0.6, seed=21)
+    Sig = oracle.sigma(oracle.covariance(st.U, st.r, st.eta))
+    for n in (5, 7, 9):
+        H = real_basis_block(oracle.sigma_inv_block(Sig, gi.random_modes(60, n, seed=n)))
+        ref, ref_abs = oracle_tor(H)
+        seen = set()
+        for level_threads in (1, 8, 64, 1 << 17):
+            ctx.set_tuning("fx", "real", 0, 0, 0, level_threads, 1, 0)
+            _, _, tor, _ = gbs.subset_sum(ctx, H, "real", "fx")
+            seen.add(tuple(tor))
+            assert abs(float(frac3(tor) - ref.to_fraction())) <= 8 * n * 2.0 ** -140 * ref_abs
+            ctx.set_tuning("fp64", "real", 0, 0, 0, level_threads, 1, 0)
+            _, _, tor, a = gbs.subset_sum(ctx, H, "real", "fp64")
+            assert abs(float(frac3(tor) - ref.to_fraction())) <= 8 * n * 2.0 ** -53 * ref_abs + 24 * 2.0 ** -53 * a
+        assert len(seen) == 1, n
+    ctx.set_tuning("fx", "real", 6, 6, 0, 1 << 18)
+    ctx.set_tuning("fp64", "real", 5, 8, 8, 1 << 17, 0, 4)
